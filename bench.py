@@ -1,0 +1,367 @@
+"""Benchmark of the PAKR expansion hot path on one or more GB300s.
+
+One step = one ``pakr_expand`` (sample, cost-pruned NN, propagate + collide,
+append) of the 3D double-integrator workload: 6D state, 50 random boxes,
+1024 parents x 8 controls = 8192 rollouts, tree prefilled to 1,000,000 nodes
+(cap 2^20).  Before each timed step the tree is truncated back to 1,000,000
+nodes and L2 is flushed (a 256 MB write), so every step does the same work
+from DRAM.
+
+Printed JSON line: tree expansions/s (rollouts per second) over all ranks,
+the NN kernel's roofline (FP32 ALU bound), the e2e rate through the C ABI with
+the per-step info read back to the host, p50 time to first solution and the
+AO-x cost after 100 ms, the CPU oracle timed on a bounded sample, clocks.
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead.
+Multi-GPU (torchrun): independent replicas, one per GPU, weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "di3"
+N_PREFILL = 1_000_000
+METRIC = "tree expansions/s"
+UNIT = "rollouts/s"
+WORKLOAD_DESC = ("3D double integrator (6D state, pos [0,1]^3, vel [-1,1]^3, accel [-1,1]^3), RK4 dt=0.05, "
+                 "1-20 substeps per edge, 50 random boxes, B=1024 parents x k=8 controls = 8192 rollouts per "
+                 "expansion, tree cap 2^20 prefilled to 1,000,000 uniform nodes, cost bound +inf")
+
+
+def _dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(local_units, local_seconds, group=None):
+    """Whole-job throughput: units summed over ranks / the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_available() or not dist.is_initialized():
+        return local_units / local_seconds, local_seconds, local_units
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM, group=group)
+    return u.item() / t.item(), t.item(), u.item()
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def nn_flops_per_launch(K, n, d):
+    """Algorithmic FP32 work of one nearest-neighbour pass: a subtract, a
+    multiply and an add per coordinate of every (query, node) pair."""
+    return 3.0 * K * n * d
+
+
+def nn_bytes_per_launch(n, d):
+    """Algorithmic DRAM bytes: every node's d coordinates and its f-cost, once."""
+    return 4.0 * n * (d + 1)
+
+
+def cpu_baseline(spec, tree, seed, target_s=10.0):
+    """The FP64 oracle, single-threaded, on a bounded sample of the workload:
+    one expansion with fewer parents on the same 1,000,000-node tree."""
+    import oracle
+    from paper_2607_03987_gb300 import workloads as W
+
+    def run(K):
+        s = W.with_sizes(spec, K=K)
+        prob = oracle.OracleProblem(s)
+        prob.set_goal(s["x_goal"])
+        ot = oracle.OracleTree.from_arrays(s["d"], s["m"], s["cap"], tree["states"], tree["controls"],
+                                           tree["parents"], tree["costs"], tree["steps"])
+        t0 = time.perf_counter()
+        oracle.expand(prob, ot, np.inf, seed)
+        return time.perf_counter() - t0
+
+    K0 = 16
+    t0 = run(K0)
+    K1 = int(max(K0, min(spec["K"], K0 * target_s / max(t0, 1e-3))))
+    t1 = run(K1) if K1 != K0 else t0
+    rollouts = K1 * spec["k"]
+    return {"value": rollouts / t1, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one expansion with {K1} of {spec['K']} parents x {spec['k']} controls on the same "
+                      f"{N_PREFILL}-node tree ({rollouts} rollouts, {t1:.1f} s single-threaded FP64)"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2607_03987_gb300 import workloads as W
+
+    spec = W.problem(WORKLOAD, env_seed=0)
+    tree = W.prefilled_tree(spec, N_PREFILL, seed=1)
+    K_sample = 64
+    s = W.with_sizes(spec, K=K_sample)
+    prob = oracle.OracleProblem(s)
+    prob.set_goal(s["x_goal"])
+    ot = oracle.OracleTree.from_arrays(s["d"], s["m"], s["cap"], tree["states"], tree["controls"], tree["parents"],
+                                       tree["costs"], tree["steps"])
+    for w in range(args.warmup):
+        ot.T.count = N_PREFILL
+        oracle.expand(prob, ot, np.inf, 1000 + w)
+    times = []
+    for st in range(args.steps):
+        ot.T.count = N_PREFILL
+        t0 = time.perf_counter()
+        oracle.expand(prob, ot, np.inf, st)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    rollouts = K_sample * s["k"] * args.steps
+    value = rollouts / total
+    sample = (f"each step one expansion with {K_sample} of {spec['K']} parents x {spec['k']} controls on the "
+              f"{N_PREFILL}-node tree, single-threaded FP64")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="pakr", choices=["pakr", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ttfs-trials", type=int, default=100)
+    ap.add_argument("--aox-trials", type=int, default=20)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = _dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    dev = local
+    torch.cuda.set_device(dev)
+
+    from paper_2607_03987_gb300 import _build, pakr
+    from paper_2607_03987_gb300 import workloads as W
+
+    _build.build()
+    spec = W.problem(WORKLOAD, env_seed=0)
+    tree = W.prefilled_tree(spec, N_PREFILL, seed=1 + rank)
+    stream = torch.cuda.current_stream(dev)
+    planner = pakr.Planner(spec, device=dev, stream=stream)
+    planner.tree_import(tree, spec["x_goal"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    R = spec["K"] * spec["k"]
+
+    def one_step(seed, info=False):
+        return planner.expand(np.inf, seed, info=info)
+
+    for w in range(args.warmup):
+        planner.tree_truncate(N_PREFILL)
+        one_step(10_000 + w)
+    torch.cuda.synchronize(dev)
+
+    # ---- device-timed steps (value) ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    planner.set_profiling(True)
+    clocks = ClockSampler(dev).start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    appended = []
+    for s in range(args.steps):
+        planner.tree_truncate(N_PREFILL)
+        flush.zero_()
+        starts[s].record(stream)
+        one_step(s)
+        ends[s].record(stream)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    local_s = sum(step_ms) / 1e3
+    kt = planner.kernel_times()
+    planner.set_profiling(False)
+    value, t_max, units = aggregate(R * args.steps, local_s)
+    launches = sum(v["launches"] for v in kt.values())
+
+    # ---- e2e through the C ABI: per-step info read back to the host ----
+    e2e_times = []
+    for s in range(args.steps):
+        planner.tree_truncate(N_PREFILL)
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        st, info = one_step(50_000 + s, info=True)
+        e2e_times.append(time.perf_counter() - t0)
+        appended.append(info["n_appended"])
+    e2e_value, _, _ = aggregate(R * args.steps, sum(e2e_times))
+
+    # ---- roofline of the dominant kernel ----
+    nn = kt["k_nn"]
+    nn_ms = nn["ms"] / max(nn["launches"], 1)
+    flops = nn_flops_per_launch(spec["K"], N_PREFILL, spec["d"])
+    peaks, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak_tflops = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops / (nn_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak_tflops, "traffic": None, "kernel": "k_nn",
+                "peak_source": f"FP32 FFMA: {props.multi_processor_count} SMs x 128 lanes x 2 flop x "
+                               f"{sm_mhz:.0f} MHz ({peak_src} max SM clock)",
+                "nn_ms_per_launch": nn_ms,
+                "nn_dram_gbs_algorithmic": nn_bytes_per_launch(N_PREFILL, spec["d"]) / (nn_ms * 1e-3) / 1e9,
+                "kernel_ms_per_step": {k: v["ms"] / max(v["launches"], 1) for k, v in kt.items()}}
+
+    # ---- planning metrics: p50 time to first solution, AO-x cost at 100 ms ----
+    plan_spec = W.problem(WORKLOAD, env_seed=0)
+    plan_planner = pakr.Planner(plan_spec, device=dev, stream=stream)
+    ttfs_dev, ttfs_host, solved = [], [], 0
+    plan_planner.plan(plan_spec["x_init"], plan_spec["x_goal"], budget_s=1.0, seed=12345, stop_at_first=True)
+    for sd in range(args.ttfs_trials):
+        t0 = time.perf_counter()
+        r = plan_planner.plan(plan_spec["x_init"], plan_spec["x_goal"], budget_s=2.0, seed=sd + 1000 * rank,
+                              stop_at_first=True)
+        th = time.perf_counter() - t0
+        if r["n_solutions"]:
+            solved += 1
+            ttfs_dev.append(r["t_first_solution_s"] * 1e3)
+            ttfs_host.append(th * 1e3)
+    costs, n_sol = [], []
+    for sd in range(args.aox_trials):
+        r = plan_planner.plan(plan_spec["x_init"], plan_spec["x_goal"], budget_s=0.1, seed=sd + 1000 * rank)
+        costs.append(r["cost"])
+        n_sol.append(r["n_solutions"])
+    plan_planner.close()
+
+    def q(v, p):
+        return float(np.percentile(v, p)) if len(v) else None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "n_tree": N_PREFILL, "parents": spec["K"],
+                       "branching": spec["k"], "rollouts_per_step": R,
+                       "l2": "flushed between timed steps (256 MB write); tree truncated back to n before each step",
+                       "parallelism": f"replicas x{ws}"},
+            "nodes_appended_per_step": float(np.mean(appended)) if appended else None,
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 256,
+                    "how": "pakr_expand with the per-step expansion info copied back and the stream "
+                           "synchronised, host wall clock; inputs (tree) resident, bound and seed are launch "
+                           "arguments"},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "p50_time_to_first_solution_ms": q(ttfs_dev, 50),
+            "time_to_first_solution_ms": {"p25": q(ttfs_dev, 25), "p50": q(ttfs_dev, 50), "p75": q(ttfs_dev, 75),
+                                          "host_p50": q(ttfs_host, 50), "trials": args.ttfs_trials,
+                                          "success_rate": solved / max(args.ttfs_trials, 1),
+                                          "workload": "same environment, fresh tree from (0.1,0.1,0.1) to the "
+                                                      "goal ball at (0.9,0.9,0.9) r=0.05, device-resident AO-x "
+                                                      "graph stopped at the first solution"},
+            "aox_path_cost_at_100ms": {"p25": q(costs, 25), "p50": q(costs, 50), "p75": q(costs, 75),
+                                       "solutions_p50": q(n_sol, 50), "trials": args.aox_trials,
+                                       "straight_line_lower_bound": float(np.linalg.norm(
+                                           plan_spec["x_goal"][:3] - plan_spec["x_init"][:3]) - plan_spec["goal_r"])},
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(spec, tree, seed=7)
+        print(json.dumps(line), flush=True)
+    planner.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,279 @@
+/*
+ * pakr.h -- C ABI of the GB300 PAKR planner.
+ *
+ * PAKR (Parallel Asymptotically Optimal Kinodynamic RRT) grows a kinodynamic
+ * RRT in batches and wraps it in the AO-x meta-algorithm (Algorithm 1 of
+ * "Fast Asymptotically Optimal Kinodynamic Planning via Vectorization").  This
+ * library runs one batched expansion iteration (SampleStates, cost-pruned
+ * NearestNeighbor, SampleControls, RK4 Propagate with a collision check at
+ * every substep, goal test, insert) as hand-written sm_103a CUDA kernels, and
+ * the AO-x loop as a device-resident CUDA graph.
+ *
+ * Conventions for every entry point:
+ *  - Host pointers are plain host memory; the library copies what it keeps.
+ *  - Device memory is either allocated by the library (cudaMalloc) or carved
+ *    from a caller buffer given in pakr_problem_desc.workspace.
+ *  - Every call returns a pakr_status; nothing is thrown or aborted across the
+ *    ABI.  A negative status is an error; pakr_last_error() returns a message
+ *    for the calling thread.
+ *  - Work is queued on the CUDA stream given at create (NULL = the legacy
+ *    default stream).  Calls that return data to host buffers synchronise
+ *    that stream; the others only enqueue.
+ *  - A planner is not thread-safe: one host thread drives it at a time.
+ *
+ * Layout on the device (Sec. IV-A "structure of arrays"): the tree is stored
+ * dimension-major, states[k * cap + i] for state coordinate k of node i, with
+ * controls, parent indices, costs-to-come, cached f-costs and edge durations in
+ * their own arrays, and a device-resident node counter.
+ */
+#ifndef PAKR_H
+#define PAKR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes.  Non-negative values are outcomes, negative values errors. */
+typedef enum pakr_status {
+    PAKR_OK = 0,                /* the call did its work */
+    PAKR_GOAL_REACHED = 1,      /* an appended child lies in the goal region (Algorithm 1, goal test) */
+    PAKR_TREE_FULL = 2,         /* some surviving children did not fit under tree_cap and were dropped */
+    PAKR_NO_ELIGIBLE = 3,       /* no tree node has f-cost below the bound; nothing was expanded */
+    PAKR_BUDGET_EXPIRED = 4,    /* pakr_plan ran out of time / iterations without any solution */
+    PAKR_ERR_INVALID_ARG = -1,  /* a bad argument (NULL, out of range, NaN, inconsistent sizes) */
+    PAKR_ERR_CUDA = -2,         /* a CUDA runtime call failed; the message names it */
+    PAKR_ERR_OOM = -3,          /* device allocation failed or the workspace is too small */
+    PAKR_ERR_TIMEOUT = -4,      /* a bounded device wait gave up */
+    PAKR_ERR_UNIMPLEMENTED = -5,/* the requested combination is not built */
+    PAKR_ERR_DEVICE = -6        /* a kernel reported an internal consistency failure */
+} pakr_status;
+
+/* System dynamics x' = f(x, u) (Eq. 1).  State / control / position sizes:
+ *   PAKR_DI2       planar double integrator [x,y,vx,vy] / [ax,ay]         d=4  m=2 p=2
+ *   PAKR_DI3       double integrator [x,y,z,vx,vy,vz] / [ax,ay,az]        d=6  m=3 p=3  (Sec. V-A item 1)
+ *   PAKR_QUAD12    quadcopter [x,y,z,phi,theta,psi,u,v,w,p,q,r] /
+ *                  [thrust, tau_x, tau_y, tau_z], body-frame velocities   d=12 m=4 p=3  (Sec. V-A item 3)
+ *   PAKR_DUBINS3D  Dubins airplane [x,y,z,yaw,pitch,v] / [yaw', pitch', v'] d=6 m=3 p=3 (Sec. V-A item 2)
+ *   PAKR_UNICYCLE1 [x,y,theta] / [v,omega]                                 d=3  m=2 p=2  (Sec. V-C item 1)
+ *   PAKR_UNICYCLE2 [x,y,theta,v,omega] / [a,alpha]                         d=5  m=2 p=2  (Sec. V-C item 2)
+ * The first p state coordinates are the position used by obstacles, goal and
+ * path-length cost. */
+typedef enum pakr_dynamics {
+    PAKR_DI2 = 0,
+    PAKR_DI3 = 1,
+    PAKR_QUAD12 = 2,
+    PAKR_DUBINS3D = 3,
+    PAKR_UNICYCLE1 = 4,
+    PAKR_UNICYCLE2 = 5
+} pakr_dynamics;
+
+/* Trajectory cost J (Sec. III: additive, e.g. path length or duration). */
+typedef enum pakr_cost {
+    PAKR_COST_PATH_LENGTH = 0,  /* sum over substeps of |p_s - p_{s-1}| */
+    PAKR_COST_DURATION = 1      /* substeps * dt */
+} pakr_cost;
+
+/* Heuristic h of the f-cost f = g + h used by the cost-bounded pruning (Sec. IV). */
+typedef enum pakr_heuristic {
+    PAKR_H_POSITION = 0,        /* max(0, |p - p_goal| - r_goal); divided by heuristic_speed for duration cost */
+    PAKR_H_FULLSTATE = 1        /* |x - x_goal| over the whole state, the formula as printed in Sec. IV */
+} pakr_heuristic;
+
+/* Per-rollout outcome of the last expansion (pakr_debug_last_expand). */
+typedef enum pakr_outcome {
+    PAKR_ROLLOUT_APPENDED = 0,  /* inserted into the tree */
+    PAKR_ROLLOUT_PRUNED = 1,    /* f-cost not below the bound */
+    PAKR_ROLLOUT_COLLIDED = 2,  /* some substep left the state box or entered an obstacle */
+    PAKR_ROLLOUT_NO_PARENT = 3, /* no eligible parent */
+    PAKR_ROLLOUT_DROPPED = 4    /* survived but the tree was full */
+} pakr_outcome;
+
+/* Problem and batch description (Sec. III problem statement; Algorithm 1
+ * inputs: batch size B = n_parents * branching, branching factor A).
+ * All host arrays are read during pakr_create only. */
+typedef struct pakr_problem_desc {
+    int32_t dynamics;           /* pakr_dynamics */
+    const float *x_lo, *x_hi;   /* d each: closed state box; a state outside it is invalid */
+    const float *u_lo, *u_hi;   /* m each: control box sampled uniformly */
+    float dt;                   /* RK4 step (s), > 0 */
+    int32_t steps_min, steps_max; /* control held for a uniform number of substeps in [min, max], 1 <= min <= max */
+    int32_t n_boxes;            /* >= 0 */
+    const float *boxes;         /* n_boxes x (lo[p], hi[p]); a position inside a closed box is invalid */
+    int32_t n_spheres;          /* >= 0 */
+    const float *spheres;       /* n_spheres x (c[p], r); a position inside a closed ball is invalid */
+    float goal_radius;          /* goal region: closed ball of this radius around the goal position */
+    int32_t cost;               /* pakr_cost */
+    int32_t heuristic;          /* pakr_heuristic */
+    float heuristic_speed;      /* speed bound for PAKR_COST_DURATION with PAKR_H_POSITION; <= 0 gives h = 0 */
+    const float *nn_weights;    /* d per-coordinate weights of the squared NN distance, NULL = all ones */
+    const float *model_params;  /* PAKR_QUAD12: mass, Ixx, Iyy, Izz, g; NULL = 1, 0.01, 0.01, 0.02, 9.81 */
+    int32_t n_parents;          /* K = nearest-neighbour queries per iteration, >= 1 */
+    int32_t branching;          /* A = controls propagated per parent, >= 1 */
+    int64_t tree_cap;           /* N = maximum tree size, >= 1, <= 2^31 - 1 */
+    int32_t device;             /* CUDA device ordinal */
+    void *cuda_stream;          /* cudaStream_t to queue work on; NULL = default stream */
+    void *workspace;            /* optional device buffer the library carves all its memory from; NULL = cudaMalloc */
+    uint64_t workspace_bytes;   /* size of workspace; see pakr_workspace_size */
+    int32_t path_cap;           /* maximum solution path length in edges kept on the device; 0 = 4096 */
+    int32_t history_cap;        /* maximum AO-x solutions recorded per plan; 0 = 1024 */
+} pakr_problem_desc;
+
+typedef struct pakr_planner pakr_planner;
+
+/* Result of one expansion.  Filled only when the caller passes a pointer. */
+typedef struct pakr_expand_info {
+    int64_t n_start;            /* tree size the batch saw (the frozen snapshot, Sec. IV-B) */
+    int64_t n_appended;
+    int64_t n_pruned;
+    int64_t n_collided;
+    int64_t n_no_parent;
+    int64_t n_dropped;
+    int32_t goal_found;
+    int32_t reserved;
+    int64_t goal_idx;           /* cheapest appended goal child (lowest index on a tie), -1 if none */
+    float goal_cost;            /* its cost-to-come */
+    uint32_t iteration;         /* expansion counter value this batch used (Philox counter word 0) */
+} pakr_expand_info;
+
+/* Tree snapshot in host memory, node-major rows.  Caller-owned buffers. */
+typedef struct pakr_tree_host {
+    int64_t capacity;           /* rows available in each array */
+    int64_t count;              /* nodes (out for export, in for import) */
+    uint32_t iteration;         /* expansion counter */
+    float *states;              /* capacity x d */
+    float *controls;            /* capacity x m (row 0, the root, is zero) */
+    int32_t *parents;           /* capacity; root = -1 */
+    float *costs;               /* capacity; cost-to-come */
+    int32_t *steps;             /* capacity; substeps of the edge into each node */
+} pakr_tree_host;
+
+/* Best path and AO-x history of pakr_plan.  Caller-owned buffers with
+ * capacities; outputs after the separator. */
+typedef struct pakr_path {
+    int32_t max_edges;          /* capacity of controls / steps; states holds max_edges + 1 rows */
+    float *states;              /* (n_edges + 1) x d, root first */
+    float *controls;            /* n_edges x m */
+    int32_t *steps;             /* n_edges */
+    int32_t max_history;        /* capacity of the history arrays */
+    double *history_time_s;     /* device time of each solution since the plan started */
+    float *history_cost;        /* c_best after each solution (strictly decreasing) */
+    int64_t *history_iteration; /* expansion iteration of each solution */
+    /* ---- outputs ---- */
+    int32_t n_edges;            /* edges of the best path; if it exceeds max_edges nothing is copied */
+    float cost;                 /* best cost found (c_best), +inf if none */
+    int32_t n_solutions;        /* AO-x solutions found */
+    int32_t n_restarts;         /* fresh trees started because the tree filled without a solution */
+    double t_first_solution_s;  /* device time to the first solution, < 0 if none */
+    double t_total_s;           /* device time of the whole plan */
+    int64_t iterations;         /* expansion iterations run */
+} pakr_path;
+
+/* Plan flags. */
+#define PAKR_PLAN_STOP_AT_FIRST 1u  /* return after the first solution (no AO-x refinement) */
+
+/* Bytes of device memory the planner needs for this description (tree, batch
+ * workspace, path / history buffers).  Does not touch the GPU. */
+pakr_status pakr_workspace_size(const pakr_problem_desc *desc, uint64_t *bytes_out);
+
+/* Validate the description, copy its host arrays, take device memory and build
+ * the kernels' launch configuration.  *out receives the planner (NULL on
+ * error).  The tree starts empty; call pakr_tree_reset or pakr_tree_import
+ * before pakr_expand. */
+pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out);
+
+/* Release device memory the library allocated, graphs and events.  A NULL
+ * planner is ignored. */
+void pakr_destroy(pakr_planner *planner);
+
+/* Message for the last error of the calling thread ("" if none). */
+const char *pakr_last_error(void);
+
+/* T <- {(x_init, -, 0)} (Algorithm 1, fresh tree): one root node with cost 0,
+ * the expansion counter set to 0, and the goal set to x_goal (d floats; its
+ * position is the centre of the goal ball, the whole state is the target of
+ * PAKR_H_FULLSTATE).  Synchronises the stream.  Returns
+ * PAKR_ERR_INVALID_ARG if x_init is not a valid state. */
+pakr_status pakr_tree_reset(pakr_planner *planner, const float *x_init, const float *x_goal);
+
+/* One batched expansion iteration (Algorithm 1 inner loop body):
+ *   1. SampleStates: n_parents states uniform in the state box, Philox4x32-10
+ *      keyed by seed with counter (iteration, i, 0xFFFFFFFF, block);
+ *   2. NearestNeighbor: for each sample the nearest node among those present at
+ *      the start of the call whose f-cost is below cost_bound (lowest index on
+ *      a tie of the FP32 squared distance);
+ *   3. SampleControls: branching controls per parent, uniform in the control
+ *      box, and a duration in [steps_min, steps_max], counter (iteration, i, j, block);
+ *   4. Propagate: RK4 with step dt for that many substeps, validity checked at
+ *      every substep;
+ *   5. prune children with f = g + h not below cost_bound (strict), drop
+ *      invalid ones, append the rest in ascending rollout order i*branching+j
+ *      (truncated at tree_cap), test the goal, and advance the counter.
+ * cost_bound may be +inf.  If info is NULL the call only enqueues the kernels
+ * and returns PAKR_OK; otherwise it synchronises the stream, fills *info and
+ * returns PAKR_NO_ELIGIBLE, PAKR_GOAL_REACHED, PAKR_TREE_FULL or PAKR_OK (in
+ * that order of precedence). */
+pakr_status pakr_expand(pakr_planner *planner, float cost_bound, uint64_t seed, pakr_expand_info *info);
+
+/* Algorithm 1 in full: AO-x replanning from x_init towards the goal ball
+ * around x_goal until budget_s of device time has passed or max_iterations
+ * expansion iterations have run (<= 0, or above 10^7: 10^7, a hard bound on the device loop).  c_best starts at
+ * +inf; each solution sets c_best to its cost, records it, extracts its path
+ * and restarts from a fresh tree, so c_best strictly decreases.  A tree that
+ * fills without a solution is restarted; a bound no node can beat ends the run.
+ * The loop runs on the device as one CUDA graph with a conditional while node
+ * (no host round trip per iteration).  Synchronises the stream and fills *out.
+ * Returns PAKR_GOAL_REACHED if any solution was found, else
+ * PAKR_BUDGET_EXPIRED (or PAKR_NO_ELIGIBLE); PAKR_ERR_INVALID_ARG for an
+ * invalid start or a path longer than out->max_edges (out->n_edges then holds
+ * the required size). */
+pakr_status pakr_plan(pakr_planner *planner, const float *x_init, const float *x_goal, double budget_s,
+                      int64_t max_iterations, uint64_t seed, uint32_t flags, pakr_path *out);
+
+/* Copy the tree to host memory (node-major).  Synchronises the stream.
+ * PAKR_ERR_INVALID_ARG if tree->capacity < the node count (tree->count then
+ * holds the count). */
+pakr_status pakr_tree_export(pakr_planner *planner, pakr_tree_host *tree);
+
+/* Keep only the first count nodes of the tree (1 <= count <= tree_cap; a
+ * count above the current size leaves the tree unchanged).  The expansion
+ * counter is not touched.  Only enqueues a one-thread kernel. */
+pakr_status pakr_tree_truncate(pakr_planner *planner, int64_t count);
+
+/* Replace the tree with a host snapshot (for resuming AO-x runs and parity
+ * checks) and set the goal to x_goal; f-costs are recomputed on the device.
+ * Synchronises the stream.  PAKR_ERR_INVALID_ARG if count is outside
+ * [1, tree_cap] or a parent index is not smaller than its node's index. */
+pakr_status pakr_tree_import(pakr_planner *planner, const pakr_tree_host *tree, const float *x_goal);
+
+/* Per-query and per-rollout records of the last pakr_expand, for parity
+ * checks: samples (n_parents x d, node-major), near (n_parents nearest-node
+ * indices, -1 if none), outcome (n_parents*branching pakr_outcome codes),
+ * controls (R x m) and steps (R).  Any pointer may be NULL.  Synchronises. */
+pakr_status pakr_debug_last_expand(pakr_planner *planner, float *samples, int32_t *near, int8_t *outcome,
+                                   float *controls, int32_t *steps);
+
+/* Per-kernel device time accumulated since profiling was last enabled, in
+ * milliseconds, measured with CUDA events on the planner's stream around each
+ * launch.  pakr_set_profiling(p, 1) clears and starts, 0 stops.  names_out
+ * (optional) receives a static string per slot.  Slots: 0 sample, 1 nearest
+ * neighbour, 2 propagate, 3 append.  launches_out counts launches per slot. */
+pakr_status pakr_set_profiling(pakr_planner *planner, int32_t enable);
+pakr_status pakr_kernel_times(pakr_planner *planner, double *ms_out, int64_t *launches_out, const char **names_out,
+                              int32_t n_slots);
+
+/* Device-side Philox4x32-10 (Salmon et al., SC'11) for n counters: out[4*t..]
+ * = Philox(ctr[4*t..], key).  Host buffers; synchronises.  Exposes the
+ * generator the kernels use so that it can be checked word for word. */
+pakr_status pakr_philox4x32_10(pakr_planner *planner, const uint32_t *ctr, const uint32_t key[2], uint32_t *out,
+                               int64_t n);
+
+/* Library version string. */
+const char *pakr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAKR_H */

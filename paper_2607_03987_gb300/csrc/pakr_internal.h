@@ -1,0 +1,143 @@
+// pakr_internal.h -- types shared by the host runtime (pakr_api.cu) and the
+// kernels (pakr_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pakr {
+
+constexpr int kMaxD = 16;
+constexpr int kMaxM = 8;
+constexpr uint64_t kNoKey = ~0ull;  // empty packed (distance | index) or (cost | index) key
+
+enum Dyn { DI2 = 0, DI3 = 1, QUAD12 = 2, DUBINS3D = 3, UNICYCLE1 = 4, UNICYCLE2 = 5, kNumDyn = 6 };
+enum Outcome { OUT_APPENDED = 0, OUT_PRUNED = 1, OUT_COLLIDED = 2, OUT_NO_PARENT = 3, OUT_DROPPED = 4 };
+enum { COST_PATH_LENGTH = 0, COST_DURATION = 1 };
+enum { H_POSITION = 0, H_FULLSTATE = 1 };
+enum { MODE_EXPAND = 0, MODE_PLAN = 1 };
+enum { ERR_PATH_CYCLE = 1, ERR_BAD_PARENT = 2 };
+
+// Problem constants, passed to every kernel by value.
+struct DevProblem {
+    int dyn, d, m, pdim;
+    float x_lo[kMaxD], x_hi[kMaxD];
+    float u_lo[kMaxM], u_hi[kMaxM];
+    float sw[kMaxD];      // square roots of the NN weights
+    float model[8];       // QUAD12: mass, Ixx, Iyy, Izz, g
+    float dt, goal_r, h_speed;
+    int s_min, s_max;
+    int n_boxes, n_spheres;
+    const float4 *boxes;  // n_boxes x 2 float4: (lo.xyz, 0), (hi.xyz, 0); unused coordinates zero
+    const float4 *spheres;// n_spheres x float4: (c.xyz, r)
+    int cost, heuristic;
+    int K, k;             // parents per iteration, controls per parent
+    int cap;              // tree capacity
+};
+
+// Dimension-major tree arrays.
+struct DevTree {
+    float *X;       // d x cap
+    float *U;       // m x cap
+    float *cost;    // cap
+    float *fcost;   // cap, cost + h(x)
+    int *parent;    // cap
+    int *steps;     // cap
+};
+
+// Per-batch workspace.
+struct DevWork {
+    float *xr;                  // d x K samples
+    unsigned long long *nn_key; // K packed (dist bits << 32 | node)
+    float *st_x;                // d x R child states
+    float *st_u;                // m x R controls
+    float *st_cost;             // R
+    float *st_f;                // R
+    int *st_steps;              // R
+    int *st_parent;             // R
+    int8_t *outcome;            // R
+    int8_t *goal;               // R
+    int *block_count;           // one per propagate block
+};
+
+// Device control block: tree counter, per-batch scalars and AO-x state.
+struct Ctl {
+    int count;               // nodes in the tree
+    unsigned int iteration;  // expansion counter (Philox counter word 0)
+    int n_start;             // snapshot of count for the current batch
+    float bound;             // cost bound of the current batch
+    unsigned long long seed;
+    unsigned long long goal_key;  // packed (cost bits << 32 | node) of the best appended goal child
+    int n_appended, n_pruned, n_collided, n_no_parent, n_dropped;
+    int err;
+    int status;              // tree_reset: 1 valid root, 0 invalid
+    int pad0;
+    float x_goal[kMaxD];
+    // AO-x plan state
+    float c_best;
+    int plan_stop;
+    long long iterations_done;
+    unsigned long long t0_ns;
+    unsigned long long t_first_ns;
+    unsigned long long t_end_ns;
+    int n_solutions;
+    int n_restarts;
+    int path_len;            // nodes on the best path (edges + 1); negative = required length when too long
+    int plan_status;         // 0 running/budget, 1 goal at stop_at_first, 3 no eligible, -1 invalid start
+};
+
+struct PlanParams {
+    float x_init[kMaxD];
+    float x_goal[kMaxD];
+    unsigned long long seed;
+    unsigned long long budget_ns;
+    long long max_iterations;
+    int stop_at_first;
+    int pad;
+};
+
+struct DevPlanBufs {
+    int *path_nodes;        // path_cap + 1
+    float *path_x;          // (path_cap + 1) x d, node-major
+    float *path_u;          // (path_cap + 1) x m
+    int *path_steps;        // path_cap + 1
+    int path_cap;           // edges
+    unsigned long long *hist_t;  // history_cap, ns since t0
+    float *hist_cost;
+    long long *hist_iter;
+    int hist_cap;
+};
+
+// Launch configuration chosen at create.
+struct LaunchCfg {
+    int nn_variant;     // 0: 64 threads x 1 query, 1: 128 x 2, 2: 256 x 4
+    int nn_threads, nn_qpt, nn_qgroups, nn_chunks;
+    int prop_threads, prop_blocks;
+    int sample_threads, sample_blocks;
+    int obs_smem_bytes; // shared memory for obstacles + goal
+};
+
+// Kernel launchers (pakr_kernels.cu).  Each returns the launch error.
+cudaError_t launch_sample(const DevProblem &P, Ctl *ctl, const DevWork &W, const LaunchCfg &L, float bound,
+                          unsigned long long seed, int mode, cudaStream_t s);
+cudaError_t launch_nn(const DevProblem &P, const Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
+                      cudaStream_t s);
+cudaError_t launch_propagate(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
+                             cudaStream_t s);
+cudaError_t launch_append(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
+                          cudaStream_t s);
+cudaError_t launch_tree_reset(const DevProblem &P, Ctl *ctl, const DevTree &T, const float *x_init_dev,
+                              cudaStream_t s);
+cudaError_t launch_import_fcost(const DevProblem &P, Ctl *ctl, const DevTree &T, int count, cudaStream_t s);
+cudaError_t launch_plan_init(const DevProblem &P, Ctl *ctl, const DevTree &T, const PlanParams *pp,
+                             cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_plan_step(const DevProblem &P, Ctl *ctl, const DevTree &T, const PlanParams *pp,
+                             const DevPlanBufs &B, cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_truncate(Ctl *ctl, int count, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int64_t n, cudaStream_t s);
+
+// Occupancy-derived sizes (pakr_kernels.cu).
+int nn_blocks_per_sm(int d, int variant);
+int prop_blocks_per_sm(int dyn, int threads, int smem);
+
+}  // namespace pakr

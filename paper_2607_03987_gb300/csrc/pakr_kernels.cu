@@ -1,0 +1,964 @@
+// pakr_kernels.cu -- sm_103a kernels of one PAKR expansion iteration
+// (Algorithm 1 inner loop) and of the device-resident AO-x loop.
+//
+//   k_sample     SampleStates: Philox4x32-10 uniform states, clears the NN keys,
+//                snapshots the tree size (the frozen snapshot of Sec. IV-B).
+//   k_nn         NearestNeighbor among nodes with f-cost below the bound:
+//                queries in registers, FP32 SoA tree tiles staged through shared
+//                memory, lexicographic (distance, index) minimum merged across
+//                node chunks with one 64-bit atomicMin per query and chunk.
+//   k_propagate  SampleControls + RK4 Propagate + per-substep validity +
+//                cost-bounded pruning + goal test, one thread per rollout,
+//                obstacles staged in shared memory.
+//   k_append     insert survivors in ascending rollout order (block counts +
+//                warp-ballot ranks), truncate at the cap, cheapest goal child.
+//   k_plan_*     AO-x bookkeeping inside a conditional-while CUDA graph.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "pakr_internal.h"
+
+namespace pakr {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit products, Weyl key schedule.
+// ---------------------------------------------------------------------------
+struct Words4 {
+    uint32_t w[4];
+};
+
+__device__ __forceinline__ Words4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                         uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    Words4 r;
+    r.w[0] = c0;
+    r.w[1] = c1;
+    r.w[2] = c2;
+    r.w[3] = c3;
+    return r;
+}
+
+// Top 24 bits as a uniform in [0, 1): exact in FP32.
+__device__ __forceinline__ float u01(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
+
+__device__ __forceinline__ float lerp_box(float lo, float hi, uint32_t w) { return __fmaf_rn(hi - lo, u01(w), lo); }
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// Dynamics x' = f(x, u) (Eq. 1) per model, FP32.
+// ---------------------------------------------------------------------------
+template <int DYN> struct Dims;
+template <> struct Dims<DI2> { static constexpr int D = 4, M = 2, PD = 2; };
+template <> struct Dims<DI3> { static constexpr int D = 6, M = 3, PD = 3; };
+template <> struct Dims<QUAD12> { static constexpr int D = 12, M = 4, PD = 3; };
+template <> struct Dims<DUBINS3D> { static constexpr int D = 6, M = 3, PD = 3; };
+template <> struct Dims<UNICYCLE1> { static constexpr int D = 3, M = 2, PD = 2; };
+template <> struct Dims<UNICYCLE2> { static constexpr int D = 5, M = 2, PD = 2; };
+
+template <int DYN>
+__device__ __forceinline__ void deriv(const float *x, const float *u, float *xd, const DevProblem &P);
+
+// Double integrator: position' = velocity, velocity' = control.
+template <>
+__device__ __forceinline__ void deriv<DI2>(const float *x, const float *u, float *xd, const DevProblem &)
+{
+    xd[0] = x[2];
+    xd[1] = x[3];
+    xd[2] = u[0];
+    xd[3] = u[1];
+}
+
+template <>
+__device__ __forceinline__ void deriv<DI3>(const float *x, const float *u, float *xd, const DevProblem &)
+{
+    xd[0] = x[3];
+    xd[1] = x[4];
+    xd[2] = x[5];
+    xd[3] = u[0];
+    xd[4] = u[1];
+    xd[5] = u[2];
+}
+
+// Quadcopter, Z-Y-X Euler angles, body-frame linear / angular velocity, thrust
+// along body z, gravity -g along world z: p' = R v, eta' = W(eta) omega,
+// v' = v x omega + R^T g + T/m e3, omega' = I^-1 (tau - omega x I omega).
+template <>
+__device__ __forceinline__ void deriv<QUAD12>(const float *x, const float *u, float *xd, const DevProblem &P)
+{
+    const float mass = P.model[0], Ixx = P.model[1], Iyy = P.model[2], Izz = P.model[3], g = P.model[4];
+    float sf, cf, st, ct, sp, cp;
+    sincosf(x[3], &sf, &cf);
+    sincosf(x[4], &st, &ct);
+    sincosf(x[5], &sp, &cp);
+    const float r00 = cp * ct, r01 = cp * st * sf - sp * cf, r02 = cp * st * cf + sp * sf;
+    const float r10 = sp * ct, r11 = sp * st * sf + cp * cf, r12 = sp * st * cf - cp * sf;
+    const float r20 = -st, r21 = ct * sf, r22 = ct * cf;
+    const float vu = x[6], vv = x[7], vw = x[8];
+    const float wp = x[9], wq = x[10], wr = x[11];
+    xd[0] = r00 * vu + r01 * vv + r02 * vw;
+    xd[1] = r10 * vu + r11 * vv + r12 * vw;
+    xd[2] = r20 * vu + r21 * vv + r22 * vw;
+    const float tt = st / ct;
+    xd[3] = wp + sf * tt * wq + cf * tt * wr;
+    xd[4] = cf * wq - sf * wr;
+    xd[5] = (sf * wq + cf * wr) / ct;
+    xd[6] = (vv * wr - vw * wq) + (-g * r20);
+    xd[7] = (vw * wp - vu * wr) + (-g * r21);
+    xd[8] = (vu * wq - vv * wp) + (-g * r22) + u[0] / mass;
+    const float Ip = Ixx * wp, Iq = Iyy * wq, Ir = Izz * wr;
+    xd[9] = (u[1] - (wq * Ir - wr * Iq)) / Ixx;
+    xd[10] = (u[2] - (wr * Ip - wp * Ir)) / Iyy;
+    xd[11] = (u[3] - (wp * Iq - wq * Ip)) / Izz;
+}
+
+// Dubins airplane: speed v along the heading given by yaw and pitch.
+template <>
+__device__ __forceinline__ void deriv<DUBINS3D>(const float *x, const float *u, float *xd, const DevProblem &)
+{
+    float sy, cy, sp, cp;
+    sincosf(x[3], &sy, &cy);
+    sincosf(x[4], &sp, &cp);
+    xd[0] = x[5] * cp * cy;
+    xd[1] = x[5] * cp * sy;
+    xd[2] = x[5] * sp;
+    xd[3] = u[0];
+    xd[4] = u[1];
+    xd[5] = u[2];
+}
+
+template <>
+__device__ __forceinline__ void deriv<UNICYCLE1>(const float *x, const float *u, float *xd, const DevProblem &)
+{
+    float s, c;
+    sincosf(x[2], &s, &c);
+    xd[0] = u[0] * c;
+    xd[1] = u[0] * s;
+    xd[2] = u[1];
+}
+
+template <>
+__device__ __forceinline__ void deriv<UNICYCLE2>(const float *x, const float *u, float *xd, const DevProblem &)
+{
+    float s, c;
+    sincosf(x[2], &s, &c);
+    xd[0] = x[3] * c;
+    xd[1] = x[3] * s;
+    xd[2] = x[4];
+    xd[3] = u[0];
+    xd[4] = u[1];
+}
+
+// Classical RK4 step with the control held (Sec. IV-A).  The stage sum is
+// accumulated in the order k1 + 2 k2 + 2 k3 + k4.
+template <int DYN>
+__device__ __forceinline__ void rk4_step(float *x, const float *u, float h, const DevProblem &P)
+{
+    constexpr int D = Dims<DYN>::D;
+    float k[D], t[D], acc[D];
+    deriv<DYN>(x, u, k, P);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        acc[a] = k[a];
+        t[a] = x[a] + 0.5f * h * k[a];
+    }
+    deriv<DYN>(t, u, k, P);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        acc[a] = acc[a] + 2.0f * k[a];
+        t[a] = x[a] + 0.5f * h * k[a];
+    }
+    deriv<DYN>(t, u, k, P);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        acc[a] = acc[a] + 2.0f * k[a];
+        t[a] = x[a] + h * k[a];
+    }
+    deriv<DYN>(t, u, k, P);
+    const float h6 = h / 6.0f;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+        x[a] = x[a] + h6 * (acc[a] + k[a]);
+}
+
+// ---------------------------------------------------------------------------
+// Validity (point robot): closed state box is valid, closed boxes and balls
+// are obstacles.  Obstacles come as padded float4 records.
+// ---------------------------------------------------------------------------
+template <int D, int PD>
+__device__ __forceinline__ bool state_valid(const float *x, const DevProblem &P, const float4 *boxes, int nb,
+                                            const float4 *spheres, int ns)
+{
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+        ok = ok && (x[a] >= P.x_lo[a]) && (x[a] <= P.x_hi[a]);
+    if (!ok)
+        return false;
+    for (int b = 0; b < nb; ++b) {
+        const float4 lo = boxes[2 * b], hi = boxes[2 * b + 1];
+        bool inside = (x[0] >= lo.x) & (x[0] <= hi.x) & (x[1] >= lo.y) & (x[1] <= hi.y);
+        if (PD > 2)
+            inside = inside & (x[2] >= lo.z) & (x[2] <= hi.z);
+        if (inside)
+            return false;
+    }
+    for (int s = 0; s < ns; ++s) {
+        const float4 c = spheres[s];
+        float dd = (x[0] - c.x) * (x[0] - c.x) + (x[1] - c.y) * (x[1] - c.y);
+        if (PD > 2)
+            dd += (x[2] - c.z) * (x[2] - c.z);
+        if (dd <= c.w * c.w)
+            return false;
+    }
+    return true;
+}
+
+// h of the f-cost (Sec. IV): distance of the position to the goal ball
+// (duration cost: divided by the speed bound), or the whole-state Euclidean
+// distance to the goal state when the full-state formula is selected.
+template <int D, int PD>
+__device__ __forceinline__ float heuristic(const float *x, const DevProblem &P, const float *goal)
+{
+    if (P.heuristic == H_FULLSTATE) {
+        float dd = 0.f;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            dd += (x[a] - goal[a]) * (x[a] - goal[a]);
+        return sqrtf(dd);
+    }
+    float dd = 0.f;
+#pragma unroll
+    for (int a = 0; a < PD; ++a)
+        dd += (x[a] - goal[a]) * (x[a] - goal[a]);
+    const float h = fmaxf(0.f, sqrtf(dd) - P.goal_r);
+    if (P.cost == COST_DURATION)
+        return P.h_speed > 0.f ? h / P.h_speed : 0.f;
+    return h;
+}
+
+template <int PD>
+__device__ __forceinline__ bool in_goal(const float *x, const DevProblem &P, const float *goal)
+{
+    float dd = 0.f;
+#pragma unroll
+    for (int a = 0; a < PD; ++a)
+        dd += (x[a] - goal[a]) * (x[a] - goal[a]);
+    return dd <= P.goal_r * P.goal_r;
+}
+
+// ---------------------------------------------------------------------------
+// k_sample: SampleStates and per-batch reset of the control block.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_sample(DevProblem P, Ctl *ctl, DevWork W, float bound, unsigned long long seed_arg, int mode)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long seed = (mode == MODE_EXPAND) ? seed_arg : ctl->seed;
+    const uint32_t it = ctl->iteration;
+    if (i < P.K) {
+        constexpr int NB = (D + 3) / 4;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const Words4 w = philox(it, (uint32_t)i, 0xFFFFFFFFu, (uint32_t)b, (uint32_t)seed, (uint32_t)(seed >> 32));
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int dim = 4 * b + t;
+                if (dim < D)
+                    W.xr[(size_t)dim * P.K + i] = lerp_box(P.x_lo[dim], P.x_hi[dim], w.w[t]);
+            }
+        }
+        W.nn_key[i] = kNoKey;
+    }
+    if (i == 0) {
+        ctl->bound = (mode == MODE_EXPAND) ? bound : ctl->c_best;
+        if (mode == MODE_EXPAND)
+            ctl->seed = seed_arg;
+        ctl->n_start = ctl->count;
+        ctl->goal_key = kNoKey;
+        ctl->n_appended = 0;
+        ctl->n_pruned = 0;
+        ctl->n_collided = 0;
+        ctl->n_no_parent = 0;
+        ctl->n_dropped = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_nn: cost-pruned brute-force nearest neighbour.
+//
+// Block (chunk c, query group g): QPT queries per thread held in registers,
+// nodes [c*per, (c+1)*per) streamed as TILE-node tiles into shared memory,
+// node-major with rows padded to DP = 4*ceil(D/4) floats so each node is read
+// with DP/4 broadcast 128-bit loads.  Ineligible nodes (f-cost not below the
+// bound) and padding get +inf in coordinate 0, so their squared distance is
+// +inf and never wins the strict comparison.  Within a thread nodes are
+// visited in ascending index order, so a strict '<' keeps the lowest index;
+// across threads and chunks the packed key (distance bits << 32 | index) is
+// merged with atomicMin, which orders by distance and then by index
+// (distances are non-negative, so their IEEE bits order like the values).
+// ---------------------------------------------------------------------------
+template <int D, int QPT, int NT, int TILE>
+__global__ void __launch_bounds__(NT) k_nn(DevProblem P, const Ctl *__restrict__ ctl, DevTree T, DevWork W)
+{
+    constexpr int DP = (D + 3) / 4 * 4;
+    constexpr int DV = DP / 4;
+    __shared__ __align__(16) float s_node[TILE * DP];
+
+    const int n = ctl->n_start;
+    const float bound = ctl->bound;
+    const int K = P.K;
+    const int cap = P.cap;
+    const int tid = threadIdx.x;
+    const int qbase = blockIdx.y * NT * QPT;
+
+    float q[QPT][D];
+    float best[QPT];
+    int bidx[QPT];
+#pragma unroll
+    for (int qi = 0; qi < QPT; ++qi) {
+        const int qid = qbase + qi * NT + tid;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            q[qi][a] = (qid < K) ? W.xr[(size_t)a * K + qid] * P.sw[a] : 0.f;
+        best[qi] = __int_as_float(0x7f800000);
+        bidx[qi] = -1;
+    }
+
+    const int nchunks = gridDim.x;
+    int per = (n + nchunks - 1) / nchunks;
+    per = (per + TILE - 1) / TILE * TILE;
+    const int start = blockIdx.x * per;
+    const int end = min(n, start + per);
+
+    for (int t0 = start; t0 < end; t0 += TILE) {
+        __syncthreads();
+        for (int e = tid; e < TILE; e += NT) {
+            const int j = t0 + e;
+            float v[DP];
+            const bool in = j < end;
+            const bool ok = in && (T.fcost[j] < bound);
+#pragma unroll
+            for (int a = 0; a < DP; ++a)
+                v[a] = (a < D && in) ? T.X[(size_t)a * cap + j] * P.sw[a] : 0.f;
+            if (!ok)
+                v[0] = __int_as_float(0x7f800000);
+            float4 *dst = reinterpret_cast<float4 *>(&s_node[e * DP]);
+#pragma unroll
+            for (int c = 0; c < DV; ++c)
+                dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+        }
+        __syncthreads();
+        const float4 *s4 = reinterpret_cast<const float4 *>(s_node);
+#pragma unroll 2
+        for (int e = 0; e < TILE; ++e) {
+            float xn[DP];
+#pragma unroll
+            for (int c = 0; c < DV; ++c) {
+                const float4 t = s4[e * DV + c];
+                xn[4 * c] = t.x;
+                xn[4 * c + 1] = t.y;
+                xn[4 * c + 2] = t.z;
+                xn[4 * c + 3] = t.w;
+            }
+#pragma unroll
+            for (int qi = 0; qi < QPT; ++qi) {
+                float diff = q[qi][0] - xn[0];
+                float acc = __fmul_rn(diff, diff);
+#pragma unroll
+                for (int a = 1; a < D; ++a) {
+                    diff = q[qi][a] - xn[a];
+                    acc = __fmaf_rn(diff, diff, acc);
+                }
+                if (acc < best[qi]) {
+                    best[qi] = acc;
+                    bidx[qi] = t0 + e;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int qi = 0; qi < QPT; ++qi) {
+        const int qid = qbase + qi * NT + tid;
+        if (qid < K && bidx[qi] >= 0) {
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(best[qi]) << 32) | (unsigned long long)(uint32_t)bidx[qi];
+            atomicMin(&W.nn_key[qid], key);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_propagate: one thread per rollout r = i*k + j.
+// ---------------------------------------------------------------------------
+template <int DYN>
+__device__ __forceinline__ int rollout(const DevProblem &P, float *x, const float *u, int S, float &g, float bound,
+                                       float &f_out, const float4 *boxes, const float4 *spheres, const float *goal)
+{
+    constexpr int D = Dims<DYN>::D, PD = Dims<DYN>::PD;
+    // f = g + h is non-decreasing along an edge for path-length cost with the
+    // position heuristic (h is 1-Lipschitz in position), so a partial f at or
+    // above the bound already decides the prune.
+    const bool early = (P.cost == COST_PATH_LENGTH) && (P.heuristic == H_POSITION);
+    if (P.cost == COST_DURATION) {
+        g = g + (float)S * P.dt;
+        if (!(g < bound))
+            return OUT_PRUNED;  // h >= 0
+    }
+    for (int s = 1; s <= S; ++s) {
+        float xp[PD];
+#pragma unroll
+        for (int a = 0; a < PD; ++a)
+            xp[a] = x[a];
+        rk4_step<DYN>(x, u, P.dt, P);
+        if (P.cost == COST_PATH_LENGTH) {
+            float dd = 0.f;
+#pragma unroll
+            for (int a = 0; a < PD; ++a)
+                dd += (x[a] - xp[a]) * (x[a] - xp[a]);
+            g += sqrtf(dd);
+        }
+        if (!state_valid<D, PD>(x, P, boxes, P.n_boxes, spheres, P.n_spheres))
+            return OUT_COLLIDED;
+        if (early && !(g + heuristic<D, PD>(x, P, goal) < bound))
+            return OUT_PRUNED;
+    }
+    f_out = g + heuristic<D, PD>(x, P, goal);
+    if (!(f_out < bound))
+        return OUT_PRUNED;
+    return OUT_APPENDED;
+}
+
+template <int DYN>
+__global__ void __launch_bounds__(256) k_propagate(DevProblem P, Ctl *ctl, DevTree T, DevWork W)
+{
+    constexpr int D = Dims<DYN>::D, M = Dims<DYN>::M, PD = Dims<DYN>::PD;
+    extern __shared__ float4 s_obs[];
+    float4 *s_box = s_obs;
+    float4 *s_sph = s_obs + 2 * P.n_boxes;
+    float *s_goal = reinterpret_cast<float *>(s_sph + P.n_spheres);
+    for (int t = threadIdx.x; t < 2 * P.n_boxes; t += blockDim.x)
+        s_box[t] = P.boxes[t];
+    for (int t = threadIdx.x; t < P.n_spheres; t += blockDim.x)
+        s_sph[t] = P.spheres[t];
+    if (threadIdx.x < D)
+        s_goal[threadIdx.x] = ctl->x_goal[threadIdx.x];
+    __syncthreads();
+
+    const int R = P.K * P.k;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    int out = -1;
+    if (r < R) {
+        const int i = r / P.k;
+        const int j = r - i * P.k;
+        const uint32_t it = ctl->iteration;
+        const unsigned long long seed = ctl->seed;
+        const float bound = ctl->bound;
+        // SampleControls: words 0..M-1 the control, word M the duration.
+        float u[M];
+        int S;
+        {
+            constexpr int NB = (M + 1 + 3) / 4;
+            uint32_t words[4 * NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const Words4 w = philox(it, (uint32_t)i, (uint32_t)j, (uint32_t)b, (uint32_t)seed,
+                                        (uint32_t)(seed >> 32));
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    words[4 * b + t] = w.w[t];
+            }
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+                u[a] = lerp_box(P.u_lo[a], P.u_hi[a], words[a]);
+            const uint64_t span = (uint64_t)(P.s_max - P.s_min + 1);
+            S = P.s_min + (int)(((uint64_t)words[M] * span) >> 32);
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+            W.st_u[(size_t)a * R + r] = u[a];
+        W.st_steps[r] = S;
+
+        const unsigned long long key = W.nn_key[i];
+        if (key == kNoKey) {
+            out = OUT_NO_PARENT;
+        } else {
+            const int par = (int)(uint32_t)(key & 0xFFFFFFFFull);
+            float x[D];
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                x[a] = T.X[(size_t)a * P.cap + par];
+            float g = T.cost[par];
+            float f = 0.f;
+            out = rollout<DYN>(P, x, u, S, g, bound, f, s_box, s_sph, s_goal);
+            if (out == OUT_APPENDED) {
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+                    W.st_x[(size_t)a * R + r] = x[a];
+                W.st_cost[r] = g;
+                W.st_f[r] = f;
+                W.st_parent[r] = par;
+                W.goal[r] = in_goal<PD>(x, P, s_goal) ? 1 : 0;
+            }
+        }
+        W.outcome[r] = (int8_t)out;
+    }
+    const int n_cand = __syncthreads_count(out == OUT_APPENDED);
+    const int n_pr = __syncthreads_count(out == OUT_PRUNED);
+    const int n_col = __syncthreads_count(out == OUT_COLLIDED);
+    const int n_np = __syncthreads_count(out == OUT_NO_PARENT);
+    if (threadIdx.x == 0) {
+        W.block_count[blockIdx.x] = n_cand;
+        if (n_pr)
+            atomicAdd(&ctl->n_pruned, n_pr);
+        if (n_col)
+            atomicAdd(&ctl->n_collided, n_col);
+        if (n_np)
+            atomicAdd(&ctl->n_no_parent, n_np);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_append: survivors of block b go to n_start + (survivors of blocks < b) +
+// (rank inside the block), i.e. ascending rollout order; positions at or past
+// the cap are dropped.  Goal children compete through atomicMin on the packed
+// (cost bits << 32 | node) key: the cheapest wins, the lowest node on a tie.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int block_sum(int v, int *s_tmp)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+        s_tmp[wid] = v;
+    __syncthreads();
+    int tot = 0;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w)
+        tot += s_tmp[w];
+    return tot;
+}
+
+template <int D, int M>
+__global__ void __launch_bounds__(256) k_append(DevProblem P, Ctl *ctl, DevTree T, DevWork W, int nblk)
+{
+    __shared__ int s_tmp[32];
+    __shared__ int s_warp[32];
+    const int R = P.K * P.k;
+    int part = 0, tot = 0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        const int c = W.block_count[b];
+        tot += c;
+        if (b < (int)blockIdx.x)
+            part += c;
+    }
+    part = block_sum(part, s_tmp);
+    tot = block_sum(tot, s_tmp);
+
+    const int n_start = ctl->n_start;
+    const int cap = P.cap;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool cand = (r < R) && (W.outcome[r] == OUT_APPENDED);
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, cand);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+        s_warp[wid] = __popc(bal);
+    __syncthreads();
+    int warp_off = 0;
+    for (int w = 0; w < wid; ++w)
+        warp_off += s_warp[w];
+    const long long pos = (long long)n_start + part + warp_off + __popc(bal & ((1u << lane) - 1u));
+    if (cand) {
+        if (pos < cap) {
+            const int p = (int)pos;
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                T.X[(size_t)a * cap + p] = W.st_x[(size_t)a * R + r];
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+                T.U[(size_t)a * cap + p] = W.st_u[(size_t)a * R + r];
+            const float c = W.st_cost[r];
+            T.cost[p] = c;
+            T.fcost[p] = W.st_f[r];
+            T.parent[p] = W.st_parent[r];
+            T.steps[p] = W.st_steps[r];
+            if (W.goal[r])
+                atomicMin(&ctl->goal_key, ((unsigned long long)__float_as_uint(c) << 32) | (unsigned long long)p);
+        } else {
+            W.outcome[r] = OUT_DROPPED;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        long long room = (long long)cap - n_start;
+        if (room < 0)
+            room = 0;
+        const int app = (int)min((long long)tot, room);
+        ctl->n_appended = app;
+        ctl->n_dropped = tot - app;
+        ctl->count = n_start + app;
+        ctl->iteration = ctl->iteration + 1u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tree reset / import / AO-x graph kernels.
+// ---------------------------------------------------------------------------
+template <int DYN>
+__global__ void k_tree_reset(DevProblem P, Ctl *ctl, DevTree T, const float *x_init)
+{
+    constexpr int D = Dims<DYN>::D, M = Dims<DYN>::M, PD = Dims<DYN>::PD;
+    if (threadIdx.x != 0 || blockIdx.x != 0)
+        return;
+    float x[D], goal[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        x[a] = x_init[a];
+        goal[a] = ctl->x_goal[a];
+        T.X[(size_t)a * P.cap] = x[a];
+    }
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+        T.U[(size_t)a * P.cap] = 0.f;
+    T.cost[0] = 0.f;
+    T.fcost[0] = heuristic<D, PD>(x, P, goal);
+    T.parent[0] = -1;
+    T.steps[0] = 0;
+    ctl->count = 1;
+    ctl->iteration = 0u;
+    ctl->err = 0;
+    ctl->status = state_valid<D, PD>(x, P, P.boxes, P.n_boxes, P.spheres, P.n_spheres) ? 1 : 0;
+}
+
+template <int DYN>
+__global__ void k_import_fcost(DevProblem P, Ctl *ctl, DevTree T, int count)
+{
+    constexpr int D = Dims<DYN>::D, PD = Dims<DYN>::PD;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= count)
+        return;
+    float x[D], goal[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        x[a] = T.X[(size_t)a * P.cap + j];
+        goal[a] = ctl->x_goal[a];
+    }
+    T.fcost[j] = T.cost[j] + heuristic<D, PD>(x, P, goal);
+}
+
+// Fresh AO-x run: goal, root, c_best = +inf, clock start.  Closes the while
+// loop before its first pass when the start is invalid or the budget is zero.
+template <int DYN>
+__global__ void k_plan_init(DevProblem P, Ctl *ctl, DevTree T, const PlanParams *pp, cudaGraphConditionalHandle h)
+{
+    constexpr int D = Dims<DYN>::D, M = Dims<DYN>::M, PD = Dims<DYN>::PD;
+    if (threadIdx.x != 0 || blockIdx.x != 0)
+        return;
+    float x[D], goal[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        x[a] = pp->x_init[a];
+        goal[a] = pp->x_goal[a];
+        ctl->x_goal[a] = goal[a];
+        T.X[(size_t)a * P.cap] = x[a];
+    }
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+        T.U[(size_t)a * P.cap] = 0.f;
+    T.cost[0] = 0.f;
+    T.fcost[0] = heuristic<D, PD>(x, P, goal);
+    T.parent[0] = -1;
+    T.steps[0] = 0;
+    ctl->count = 1;
+    ctl->iteration = 0u;
+    ctl->seed = pp->seed;
+    ctl->c_best = __int_as_float(0x7f800000);
+    ctl->iterations_done = 0;
+    ctl->n_solutions = 0;
+    ctl->n_restarts = 0;
+    ctl->path_len = 0;
+    ctl->err = 0;
+    ctl->t_first_ns = ~0ull;
+    const bool valid = state_valid<D, PD>(x, P, P.boxes, P.n_boxes, P.spheres, P.n_spheres);
+    ctl->plan_status = valid ? 0 : -1;
+    const bool run = valid && pp->max_iterations > 0 && pp->budget_ns > 0;
+    ctl->plan_stop = run ? 0 : 1;
+    const unsigned long long now = globaltimer_ns();
+    ctl->t0_ns = now;
+    ctl->t_end_ns = now;
+    cudaGraphSetConditional(h, run ? 1u : 0u);
+}
+
+// End of one AO-x loop pass: record a solution (c_best, history, path) and
+// restart from the root, restart a full tree, stop on budget / iterations /
+// no eligible node.  One warp: lane 0 chases parents, the warp gathers rows.
+template <int D, int M>
+__global__ void k_plan_step(DevProblem P, Ctl *ctl, DevTree T, const PlanParams *pp, DevPlanBufs B,
+                            cudaGraphConditionalHandle h)
+{
+    __shared__ int s_len;
+    __shared__ int s_found;
+    const int lane = threadIdx.x;
+    if (lane == 0) {
+        const unsigned long long now = globaltimer_ns();
+        ctl->iterations_done += 1;
+        const unsigned long long key = ctl->goal_key;
+        s_found = 0;
+        s_len = 0;
+        if (key != kNoKey) {
+            const float c = __uint_as_float((uint32_t)(key >> 32));
+            const int node = (int)(uint32_t)(key & 0xFFFFFFFFull);
+            ctl->c_best = c;
+            const int ns = ctl->n_solutions;
+            if (ns < B.hist_cap) {
+                B.hist_t[ns] = now - ctl->t0_ns;
+                B.hist_cost[ns] = c;
+                B.hist_iter[ns] = ctl->iterations_done - 1;
+            }
+            if (ns == 0)
+                ctl->t_first_ns = now - ctl->t0_ns;
+            ctl->n_solutions = ns + 1;
+            // ExtractPath: length first, bounded by the node count.
+            int len = 0;
+            const int limit = ctl->count + 1;
+            for (int v = node; v >= 0 && len <= limit; v = T.parent[v])
+                ++len;
+            if (len > limit) {
+                ctl->err |= ERR_PATH_CYCLE;
+                ctl->path_len = 0;
+            } else if (len > B.path_cap + 1) {
+                ctl->path_len = -len;
+            } else {
+                int at = len - 1;
+                for (int v = node; v >= 0; v = T.parent[v])
+                    B.path_nodes[at--] = v;
+                ctl->path_len = len;
+                s_len = len;
+            }
+            s_found = 1;
+        }
+    }
+    __syncwarp();
+    const int len = s_len;
+    for (int t = lane; t < len; t += 32) {
+        const int v = B.path_nodes[t];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            B.path_x[(size_t)t * D + a] = T.X[(size_t)a * P.cap + v];
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+            B.path_u[(size_t)t * M + a] = T.U[(size_t)a * P.cap + v];
+        B.path_steps[t] = T.steps[v];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        const unsigned long long now = globaltimer_ns();
+        bool stop = false;
+        bool restart = false;
+        if (s_found) {
+            restart = true;
+            if (pp->stop_at_first) {
+                stop = true;
+                ctl->plan_status = 1;
+            }
+        } else if (ctl->count >= P.cap) {
+            restart = true;
+            ctl->n_restarts += 1;
+        }
+        if (!s_found && ctl->n_no_parent >= P.K * P.k) {
+            stop = true;
+            ctl->plan_status = 3;
+        }
+        if (now - ctl->t0_ns >= pp->budget_ns || ctl->iterations_done >= pp->max_iterations)
+            stop = true;
+        if (restart)
+            ctl->count = 1;
+        ctl->plan_stop = stop ? 1 : 0;
+        ctl->t_end_ns = now;
+        cudaGraphSetConditional(h, stop ? 0u : 1u);
+    }
+}
+
+__global__ void k_truncate(Ctl *ctl, int count)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0 && count < ctl->count)
+        ctl->count = count;
+}
+
+__global__ void k_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int64_t n)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n)
+        return;
+    const Words4 w = philox(ctr[4 * t], ctr[4 * t + 1], ctr[4 * t + 2], ctr[4 * t + 3], k0, k1);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+        out[4 * t + a] = w.w[a];
+}
+
+// ---------------------------------------------------------------------------
+// Launchers and dispatch.
+// ---------------------------------------------------------------------------
+#define PAKR_DISPATCH_DYN(dyn, BODY)                                                                                   \
+    switch (dyn) {                                                                                                     \
+    case DI2: { constexpr int DYN_ = DI2; BODY; } break;                                                               \
+    case DI3: { constexpr int DYN_ = DI3; BODY; } break;                                                               \
+    case QUAD12: { constexpr int DYN_ = QUAD12; BODY; } break;                                                         \
+    case DUBINS3D: { constexpr int DYN_ = DUBINS3D; BODY; } break;                                                     \
+    case UNICYCLE1: { constexpr int DYN_ = UNICYCLE1; BODY; } break;                                                   \
+    case UNICYCLE2: { constexpr int DYN_ = UNICYCLE2; BODY; } break;                                                   \
+    default: return cudaErrorInvalidValue;                                                                             \
+    }
+
+constexpr int kNnTile = 256;
+
+cudaError_t launch_sample(const DevProblem &P, Ctl *ctl, const DevWork &W, const LaunchCfg &L, float bound,
+                          unsigned long long seed, int mode, cudaStream_t s)
+{
+    PAKR_DISPATCH_DYN(P.dyn, (k_sample<Dims<DYN_>::D><<<L.sample_blocks, L.sample_threads, 0, s>>>(
+                                 P, ctl, W, bound, seed, mode)));
+    return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t launch_nn_d(const DevProblem &P, const Ctl *ctl, const DevTree &T, const DevWork &W,
+                               const LaunchCfg &L, cudaStream_t s)
+{
+    const dim3 grid(L.nn_chunks, L.nn_qgroups);
+    switch (L.nn_variant) {
+    case 0: k_nn<D, 1, 64, kNnTile><<<grid, 64, 0, s>>>(P, ctl, T, W); break;
+    case 1: k_nn<D, 2, 128, kNnTile><<<grid, 128, 0, s>>>(P, ctl, T, W); break;
+    default: k_nn<D, 4, 256, kNnTile><<<grid, 256, 0, s>>>(P, ctl, T, W); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nn(const DevProblem &P, const Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
+                      cudaStream_t s)
+{
+    PAKR_DISPATCH_DYN(P.dyn, return launch_nn_d<Dims<DYN_>::D>(P, ctl, T, W, L, s));
+    return cudaSuccess;
+}
+
+cudaError_t launch_propagate(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
+                             cudaStream_t s)
+{
+    PAKR_DISPATCH_DYN(P.dyn, (k_propagate<DYN_><<<L.prop_blocks, L.prop_threads, L.obs_smem_bytes, s>>>(
+                                 P, ctl, T, W)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_append(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
+                          cudaStream_t s)
+{
+    PAKR_DISPATCH_DYN(P.dyn, (k_append<Dims<DYN_>::D, Dims<DYN_>::M><<<L.prop_blocks, L.prop_threads, 0, s>>>(
+                                 P, ctl, T, W, L.prop_blocks)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tree_reset(const DevProblem &P, Ctl *ctl, const DevTree &T, const float *x_init_dev,
+                              cudaStream_t s)
+{
+    PAKR_DISPATCH_DYN(P.dyn, (k_tree_reset<DYN_><<<1, 32, 0, s>>>(P, ctl, T, x_init_dev)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import_fcost(const DevProblem &P, Ctl *ctl, const DevTree &T, int count, cudaStream_t s)
+{
+    const int blocks = (count + 255) / 256;
+    PAKR_DISPATCH_DYN(P.dyn, (k_import_fcost<DYN_><<<blocks, 256, 0, s>>>(P, ctl, T, count)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan_init(const DevProblem &P, Ctl *ctl, const DevTree &T, const PlanParams *pp,
+                             cudaGraphConditionalHandle h, cudaStream_t s)
+{
+    PAKR_DISPATCH_DYN(P.dyn, (k_plan_init<DYN_><<<1, 32, 0, s>>>(P, ctl, T, pp, h)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan_step(const DevProblem &P, Ctl *ctl, const DevTree &T, const PlanParams *pp,
+                             const DevPlanBufs &B, cudaGraphConditionalHandle h, cudaStream_t s)
+{
+    PAKR_DISPATCH_DYN(P.dyn, (k_plan_step<Dims<DYN_>::D, Dims<DYN_>::M><<<1, 32, 0, s>>>(P, ctl, T, pp, B, h)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_truncate(Ctl *ctl, int count, cudaStream_t s)
+{
+    k_truncate<<<1, 32, 0, s>>>(ctl, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int64_t n, cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    const int64_t blocks = (n + 255) / 256;
+    k_philox<<<(unsigned)blocks, 256, 0, s>>>(ctr, k0, k1, out, n);
+    return cudaGetLastError();
+}
+
+template <int D>
+static int nn_occ(int variant)
+{
+    int nb = 0;
+    switch (variant) {
+    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nn<D, 1, 64, kNnTile>, 64, 0); break;
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nn<D, 2, 128, kNnTile>, 128, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nn<D, 4, 256, kNnTile>, 256, 0); break;
+    }
+    return nb;
+}
+
+int nn_blocks_per_sm(int d, int variant)
+{
+    switch (d) {
+    case 3: return nn_occ<3>(variant);
+    case 4: return nn_occ<4>(variant);
+    case 5: return nn_occ<5>(variant);
+    case 6: return nn_occ<6>(variant);
+    case 12: return nn_occ<12>(variant);
+    default: return 0;
+    }
+}
+
+int prop_blocks_per_sm(int dyn, int threads, int smem)
+{
+    int nb = 0;
+    switch (dyn) {
+    case DI2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<DI2>, threads, smem); break;
+    case DI3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<DI3>, threads, smem); break;
+    case QUAD12: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<QUAD12>, threads, smem); break;
+    case DUBINS3D: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<DUBINS3D>, threads, smem); break;
+    case UNICYCLE1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<UNICYCLE1>, threads, smem); break;
+    case UNICYCLE2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<UNICYCLE2>, threads, smem); break;
+    default: break;
+    }
+    return nb;
+}
+
+}  // namespace pakr

@@ -1,0 +1,333 @@
+"""Python binding of the C ABI in include/pakr.h (argument marshalling only).
+
+Every step of the planner runs in libpakr.so's CUDA kernels; this module only
+converts numpy / torch arguments to the ABI's plain pointers and sizes.  PyTorch
+provides the device memory (the planner's workspace is a torch tensor) and the
+stream (the current torch stream at creation).  If libpakr.so is missing or
+fails to load, every entry point raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libpakr.so")
+
+# status codes
+OK, GOAL_REACHED, TREE_FULL, NO_ELIGIBLE, BUDGET_EXPIRED = 0, 1, 2, 3, 4
+ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_UNIMPLEMENTED, ERR_DEVICE = -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "OK", 1: "GOAL_REACHED", 2: "TREE_FULL", 3: "NO_ELIGIBLE", 4: "BUDGET_EXPIRED",
+                -1: "ERR_INVALID_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_TIMEOUT",
+                -5: "ERR_UNIMPLEMENTED", -6: "ERR_DEVICE"}
+# dynamics / cost / heuristic / outcome / flags
+DI2, DI3, QUAD12, DUBINS3D, UNICYCLE1, UNICYCLE2 = range(6)
+COST_PATH_LENGTH, COST_DURATION = 0, 1
+H_POSITION, H_FULLSTATE = 0, 1
+ROLLOUT_APPENDED, ROLLOUT_PRUNED, ROLLOUT_COLLIDED, ROLLOUT_NO_PARENT, ROLLOUT_DROPPED = range(5)
+PLAN_STOP_AT_FIRST = 1
+
+_PF = C.POINTER(C.c_float)
+_PI32 = C.POINTER(C.c_int32)
+_PI64 = C.POINTER(C.c_int64)
+_PD = C.POINTER(C.c_double)
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [
+        ("dynamics", C.c_int32),
+        ("x_lo", _PF), ("x_hi", _PF), ("u_lo", _PF), ("u_hi", _PF),
+        ("dt", C.c_float), ("steps_min", C.c_int32), ("steps_max", C.c_int32),
+        ("n_boxes", C.c_int32), ("boxes", _PF),
+        ("n_spheres", C.c_int32), ("spheres", _PF),
+        ("goal_radius", C.c_float),
+        ("cost", C.c_int32), ("heuristic", C.c_int32), ("heuristic_speed", C.c_float),
+        ("nn_weights", _PF), ("model_params", _PF),
+        ("n_parents", C.c_int32), ("branching", C.c_int32),
+        ("tree_cap", C.c_int64), ("device", C.c_int32), ("cuda_stream", C.c_void_p),
+        ("workspace", C.c_void_p), ("workspace_bytes", C.c_uint64),
+        ("path_cap", C.c_int32), ("history_cap", C.c_int32),
+    ]
+
+
+class ExpandInfo(C.Structure):
+    _fields_ = [
+        ("n_start", C.c_int64), ("n_appended", C.c_int64), ("n_pruned", C.c_int64),
+        ("n_collided", C.c_int64), ("n_no_parent", C.c_int64), ("n_dropped", C.c_int64),
+        ("goal_found", C.c_int32), ("reserved", C.c_int32), ("goal_idx", C.c_int64),
+        ("goal_cost", C.c_float), ("iteration", C.c_uint32),
+    ]
+
+
+class TreeHost(C.Structure):
+    _fields_ = [
+        ("capacity", C.c_int64), ("count", C.c_int64), ("iteration", C.c_uint32),
+        ("states", _PF), ("controls", _PF), ("parents", _PI32), ("costs", _PF), ("steps", _PI32),
+    ]
+
+
+class Path(C.Structure):
+    _fields_ = [
+        ("max_edges", C.c_int32), ("states", _PF), ("controls", _PF), ("steps", _PI32),
+        ("max_history", C.c_int32), ("history_time_s", _PD), ("history_cost", _PF),
+        ("history_iteration", _PI64),
+        ("n_edges", C.c_int32), ("cost", C.c_float), ("n_solutions", C.c_int32), ("n_restarts", C.c_int32),
+        ("t_first_solution_s", C.c_double), ("t_total_s", C.c_double), ("iterations", C.c_int64),
+    ]
+
+
+EXPORTED = [
+    "pakr_workspace_size", "pakr_create", "pakr_destroy", "pakr_last_error", "pakr_tree_reset",
+    "pakr_expand", "pakr_plan", "pakr_tree_export", "pakr_tree_import", "pakr_tree_truncate", "pakr_debug_last_expand",
+    "pakr_set_profiling", "pakr_kernel_times", "pakr_philox4x32_10", "pakr_version",
+]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libpakr.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    L = C.CDLL(_LIB_PATH)
+    L.pakr_workspace_size.argtypes = [C.POINTER(ProblemDesc), C.POINTER(C.c_uint64)]
+    L.pakr_create.argtypes = [C.POINTER(ProblemDesc), C.POINTER(C.c_void_p)]
+    L.pakr_destroy.argtypes = [C.c_void_p]
+    L.pakr_destroy.restype = None
+    L.pakr_last_error.argtypes = []
+    L.pakr_last_error.restype = C.c_char_p
+    L.pakr_version.restype = C.c_char_p
+    L.pakr_tree_reset.argtypes = [C.c_void_p, _PF, _PF]
+    L.pakr_expand.argtypes = [C.c_void_p, C.c_float, C.c_uint64, C.POINTER(ExpandInfo)]
+    L.pakr_plan.argtypes = [C.c_void_p, _PF, _PF, C.c_double, C.c_int64, C.c_uint64, C.c_uint32, C.POINTER(Path)]
+    L.pakr_tree_export.argtypes = [C.c_void_p, C.POINTER(TreeHost)]
+    L.pakr_tree_import.argtypes = [C.c_void_p, C.POINTER(TreeHost), _PF]
+    L.pakr_tree_truncate.argtypes = [C.c_void_p, C.c_int64]
+    L.pakr_debug_last_expand.argtypes = [C.c_void_p, _PF, _PI32, C.POINTER(C.c_int8), _PF, _PI32]
+    L.pakr_set_profiling.argtypes = [C.c_void_p, C.c_int32]
+    L.pakr_kernel_times.argtypes = [C.c_void_p, _PD, _PI64, C.POINTER(C.c_char_p), C.c_int32]
+    L.pakr_philox4x32_10.argtypes = [C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                     C.POINTER(C.c_uint32), C.c_int64]
+    for name in EXPORTED:
+        fn = getattr(L, name)
+        if fn.restype is C.c_int or name in ("pakr_workspace_size",):
+            fn.restype = C.c_int
+    _lib = L
+    return L
+
+
+class PakrError(RuntimeError):
+    def __init__(self, status, where):
+        msg = lib().pakr_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st, where):
+    if st < 0:
+        raise PakrError(st, where)
+    return st
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _pf(a):
+    return a.ctypes.data_as(_PF)
+
+
+class Planner:
+    """One planning problem on one GPU (a pakr_planner handle).
+
+    ``spec`` is a problem dict as produced by ``workloads.problem``.  Device
+    memory comes from a torch uint8 tensor sized by pakr_workspace_size; work
+    is queued on torch's current stream of the device.
+    """
+
+    def __init__(self, spec, device=0, stream=None, path_cap=4096, history_cap=1024, torch_workspace=True):
+        import torch
+
+        self.spec = spec
+        self.d, self.m = spec["d"], spec["m"]
+        self.K, self.k = spec["K"], spec["k"]
+        self.cap = spec["cap"]
+        self.device = device
+        self._keep = []
+        keep = self._keep
+
+        def arr(v):
+            a = _f32(v).reshape(-1)
+            keep.append(a)
+            return _pf(a)
+
+        desc = ProblemDesc()
+        desc.dynamics = spec["dyn"]
+        desc.x_lo, desc.x_hi = arr(spec["x_lo"]), arr(spec["x_hi"])
+        desc.u_lo, desc.u_hi = arr(spec["u_lo"]), arr(spec["u_hi"])
+        desc.dt = spec["dt"]
+        desc.steps_min, desc.steps_max = spec["s_min"], spec["s_max"]
+        boxes = np.asarray(spec["boxes"]).reshape(-1)
+        spheres = np.asarray(spec["spheres"]).reshape(-1)
+        desc.n_boxes = int(np.asarray(spec["boxes"]).shape[0])
+        desc.boxes = arr(boxes) if boxes.size else None
+        desc.n_spheres = int(np.asarray(spec["spheres"]).shape[0])
+        desc.spheres = arr(spheres) if spheres.size else None
+        desc.goal_radius = spec["goal_r"]
+        desc.cost = spec.get("cost", COST_PATH_LENGTH)
+        desc.heuristic = spec.get("heuristic", H_POSITION)
+        desc.heuristic_speed = spec.get("h_speed", 0.0)
+        desc.nn_weights = arr(spec["nn_w"]) if spec.get("nn_w") is not None else None
+        desc.model_params = arr(spec["model"]) if spec["dyn"] == QUAD12 else None
+        desc.n_parents, desc.branching = self.K, self.k
+        desc.tree_cap = self.cap
+        desc.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        desc.cuda_stream = C.c_void_p(stream.cuda_stream)
+        desc.path_cap = path_cap
+        desc.history_cap = history_cap
+        self.path_cap = path_cap
+        self.history_cap = history_cap
+        self.workspace = None
+        if torch_workspace:
+            nbytes = C.c_uint64()
+            _check(lib().pakr_workspace_size(C.byref(desc), C.byref(nbytes)), "pakr_workspace_size")
+            self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=f"cuda:{device}")
+            desc.workspace = C.c_void_p(self.workspace.data_ptr())
+            desc.workspace_bytes = int(nbytes.value)
+        self.desc = desc
+        h = C.c_void_p()
+        _check(lib().pakr_create(C.byref(desc), C.byref(h)), "pakr_create")
+        self.h = h
+
+    # -- lifecycle -------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().pakr_destroy(self.h)
+            self.h = None
+        self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- entry points ----------------------------------------------------
+    def tree_reset(self, x_init, x_goal):
+        xi, xg = _f32(x_init), _f32(x_goal)
+        return _check(lib().pakr_tree_reset(self.h, _pf(xi), _pf(xg)), "pakr_tree_reset")
+
+    def expand(self, bound=np.inf, seed=0, info=True):
+        if not info:
+            return _check(lib().pakr_expand(self.h, float(bound), int(seed), None), "pakr_expand"), None
+        inf = ExpandInfo()
+        st = _check(lib().pakr_expand(self.h, float(bound), int(seed), C.byref(inf)), "pakr_expand")
+        return st, {f: getattr(inf, f) for f, _ in ExpandInfo._fields_ if f != "reserved"}
+
+    def plan(self, x_init, x_goal, budget_s=1.0, max_iterations=0, seed=0, stop_at_first=False, max_edges=None,
+             max_history=None):
+        max_edges = self.path_cap if max_edges is None else max_edges
+        max_history = self.history_cap if max_history is None else max_history
+        xi, xg = _f32(x_init), _f32(x_goal)
+        p = Path()
+        states = np.zeros((max_edges + 1, self.d), np.float32)
+        controls = np.zeros((max(max_edges, 1), self.m), np.float32)
+        steps = np.zeros(max(max_edges, 1), np.int32)
+        ht = np.zeros(max(max_history, 1), np.float64)
+        hc = np.zeros(max(max_history, 1), np.float32)
+        hi = np.zeros(max(max_history, 1), np.int64)
+        p.max_edges = max_edges
+        p.states, p.controls, p.steps = _pf(states), _pf(controls), steps.ctypes.data_as(_PI32)
+        p.max_history = max_history
+        p.history_time_s, p.history_cost = ht.ctypes.data_as(_PD), _pf(hc)
+        p.history_iteration = hi.ctypes.data_as(_PI64)
+        flags = PLAN_STOP_AT_FIRST if stop_at_first else 0
+        st = _check(lib().pakr_plan(self.h, _pf(xi), _pf(xg), float(budget_s), int(max_iterations), int(seed), flags,
+                                    C.byref(p)), "pakr_plan")
+        ne = p.n_edges
+        ns = min(p.n_solutions, max_history)
+        return dict(status=st, cost=p.cost, n_edges=ne, n_solutions=p.n_solutions, n_restarts=p.n_restarts,
+                    t_first_solution_s=p.t_first_solution_s, t_total_s=p.t_total_s, iterations=p.iterations,
+                    states=states[: ne + 1].copy() if p.n_solutions else states[:0].copy(),
+                    controls=controls[:ne].copy(), steps=steps[:ne].copy(),
+                    history_time_s=ht[:ns].copy(), history_cost=hc[:ns].copy(), history_iteration=hi[:ns].copy())
+
+    def tree_export(self):
+        t = TreeHost()
+        t.capacity = 0
+        st = lib().pakr_tree_export(self.h, C.byref(t))
+        n = int(t.count)
+        if st < 0 and n == 0:
+            _check(st, "pakr_tree_export")
+        states = np.zeros((max(n, 1), self.d), np.float32)
+        controls = np.zeros((max(n, 1), self.m), np.float32)
+        parents = np.zeros(max(n, 1), np.int32)
+        costs = np.zeros(max(n, 1), np.float32)
+        steps = np.zeros(max(n, 1), np.int32)
+        t.capacity = n
+        t.states, t.controls, t.costs = _pf(states), _pf(controls), _pf(costs)
+        t.parents, t.steps = parents.ctypes.data_as(_PI32), steps.ctypes.data_as(_PI32)
+        _check(lib().pakr_tree_export(self.h, C.byref(t)), "pakr_tree_export")
+        n = int(t.count)
+        return dict(states=states[:n], controls=controls[:n], parents=parents[:n], costs=costs[:n],
+                    steps=steps[:n], count=n, iteration=int(t.iteration))
+
+    def tree_import(self, tree, x_goal):
+        n = int(tree["count"])
+        states = _f32(tree["states"]).reshape(n, self.d)
+        controls = _f32(tree["controls"]).reshape(n, self.m)
+        parents = np.ascontiguousarray(np.asarray(tree["parents"], dtype=np.int32))
+        costs = _f32(tree["costs"])
+        steps = np.ascontiguousarray(np.asarray(tree["steps"], dtype=np.int32))
+        t = TreeHost()
+        t.capacity, t.count, t.iteration = n, n, int(tree.get("iteration", 0))
+        t.states, t.controls, t.costs = _pf(states), _pf(controls), _pf(costs)
+        t.parents, t.steps = parents.ctypes.data_as(_PI32), steps.ctypes.data_as(_PI32)
+        xg = _f32(x_goal)
+        return _check(lib().pakr_tree_import(self.h, C.byref(t), _pf(xg)), "pakr_tree_import")
+
+    def tree_truncate(self, count):
+        return _check(lib().pakr_tree_truncate(self.h, int(count)), "pakr_tree_truncate")
+
+    def debug_last_expand(self):
+        K, R = self.K, self.K * self.k
+        samples = np.zeros((K, self.d), np.float32)
+        near = np.zeros(K, np.int32)
+        outcome = np.zeros(R, np.int8)
+        controls = np.zeros((R, self.m), np.float32)
+        steps = np.zeros(R, np.int32)
+        _check(lib().pakr_debug_last_expand(self.h, _pf(samples), near.ctypes.data_as(_PI32),
+                                            outcome.ctypes.data_as(C.POINTER(C.c_int8)), _pf(controls),
+                                            steps.ctypes.data_as(_PI32)), "pakr_debug_last_expand")
+        return dict(samples=samples, near=near, outcome=outcome, controls=controls, steps=steps)
+
+    def set_profiling(self, enable):
+        return _check(lib().pakr_set_profiling(self.h, int(bool(enable))), "pakr_set_profiling")
+
+    def kernel_times(self):
+        ms = (C.c_double * 4)()
+        n = (C.c_int64 * 4)()
+        names = (C.c_char_p * 4)()
+        _check(lib().pakr_kernel_times(self.h, ms, n, names, 4), "pakr_kernel_times")
+        return {names[i].decode(): dict(ms=ms[i], launches=int(n[i])) for i in range(4)}
+
+    def philox(self, ctr, key):
+        ctr = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+        k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(2))
+        out = np.zeros_like(ctr)
+        P32 = C.POINTER(C.c_uint32)
+        _check(lib().pakr_philox4x32_10(self.h, ctr.ctypes.data_as(P32), k.ctypes.data_as(P32),
+                                        out.ctypes.data_as(P32), ctr.shape[0]), "pakr_philox4x32_10")
+        return out

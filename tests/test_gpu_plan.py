@@ -1,0 +1,101 @@
+"""AO-x loop on the device (one CUDA graph) vs the oracle's AO-x loop."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_03987_gb300 import pakr
+from paper_2607_03987_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_plan(spec, seed, iters, stop_at_first=False):
+    prob = oracle.OracleProblem(spec)
+    prob.set_goal(spec["x_goal"])
+    t = oracle.OracleTree(spec["d"], spec["m"], spec["cap"])
+    return oracle.plan(prob, t, spec["x_init"], seed, iters, stop_at_first=stop_at_first)
+
+
+def check_path_properties(spec, res):
+    """Properties any returned path has: starts at x_init, ends in the goal
+    ball, durations / controls in range, c_best strictly decreasing."""
+    if res["n_solutions"] == 0:
+        return
+    s = res["states"]
+    assert np.allclose(s[0], spec["x_init"])
+    pd = spec["pdim"]
+    assert np.linalg.norm(s[-1][:pd] - spec["x_goal"][:pd]) <= spec["goal_r"] * (1 + 1e-5)
+    assert np.all((res["steps"] >= spec["s_min"]) & (res["steps"] <= spec["s_max"]))
+    assert np.all((res["controls"] >= spec["u_lo"]) & (res["controls"] <= spec["u_hi"]))
+    hc = res["history_cost"]
+    assert np.all(np.diff(hc) < 0), hc
+    assert abs(hc[-1] - res["cost"]) <= 1e-6 * max(1, res["cost"])
+    # path-length cost is at least the straight-line distance start -> goal ball
+    lb = np.linalg.norm(spec["x_goal"][:pd] - spec["x_init"][:pd]) - spec["goal_r"]
+    assert res["cost"] >= lb * (1 - 1e-5)
+
+
+@pytest.mark.parametrize("name,iters", [("di2", 40), ("di3", 12)])
+def test_plan_matches_oracle(cuda_lib, name, iters):
+    spec = W.problem(name, env_seed=0)
+    if name == "di3":
+        spec = W.with_sizes(spec, cap=200000)
+    planner = pakr.Planner(spec)
+    compared = 0
+    for seed in range(3):
+        g = planner.plan(spec["x_init"], spec["x_goal"], budget_s=60.0, max_iterations=iters, seed=seed)
+        o = oracle_plan(spec, seed, iters)
+        check_path_properties(spec, g)
+        frag = o["fragile_iteration"]
+        upto = iters if frag < 0 else frag
+        og = [(c, i) for c, i in zip(o["hist_cost"], o["hist_iter"]) if i < upto]
+        gg = [(c, i) for c, i in zip(g["history_cost"], g["history_iteration"]) if i < upto]
+        assert len(og) == len(gg), (seed, og, gg, frag)
+        for (oc, oi), (gc, gi) in zip(og, gg):
+            assert oi == gi
+            assert abs(gc - oc) <= 1e-5 * max(1, oc)
+        compared += len(og)
+        if frag < 0:
+            assert g["iterations"] == o["iterations"]
+            assert g["n_solutions"] == o["n_solutions"]
+            if o["n_solutions"]:
+                assert len(g["states"]) == len(o["path_states"])
+                assert np.allclose(g["states"], o["path_states"], rtol=1e-5, atol=1e-5)
+    planner.close()
+
+
+def test_plan_stop_at_first_and_budget(cuda_lib):
+    spec = W.problem("di3", env_seed=1)
+    planner = pakr.Planner(spec)
+    r = planner.plan(spec["x_init"], spec["x_goal"], budget_s=5.0, seed=3, stop_at_first=True)
+    assert r["status"] == pakr.GOAL_REACHED and r["n_solutions"] == 1
+    assert 0 < r["t_first_solution_s"] <= r["t_total_s"] < 5.0
+    check_path_properties(spec, r)
+    r = planner.plan(spec["x_init"], spec["x_goal"], budget_s=0.05, seed=3)
+    assert r["t_total_s"] < 0.5
+    check_path_properties(spec, r)
+    r = planner.plan(spec["x_init"], spec["x_goal"], budget_s=10.0, max_iterations=1, seed=3)
+    assert r["iterations"] == 1
+    planner.close()
+
+
+def test_plan_invalid_start(cuda_lib):
+    spec = W.problem("di2", env_seed=0)
+    planner = pakr.Planner(spec)
+    bad = spec["x_init"].copy()
+    bad[0] = 2.0  # outside the state box
+    with pytest.raises(pakr.PakrError) as e:
+        planner.plan(bad, spec["x_goal"], budget_s=1.0, seed=0)
+    assert e.value.status == pakr.ERR_INVALID_ARG
+    with pytest.raises(pakr.PakrError):
+        planner.tree_reset(bad, spec["x_goal"])
+    planner.close()
+
+
+def test_plan_quadrotor_runs(cuda_lib):
+    spec = W.problem("quad12", env_seed=0)
+    planner = pakr.Planner(spec)
+    r = planner.plan(spec["x_init"], spec["x_goal"], budget_s=2.0, seed=0)
+    assert r["iterations"] > 0
+    check_path_properties(spec, r)
+    planner.close()
