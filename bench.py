@@ -210,6 +210,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ttfs-trials", type=int, default=100)
     ap.add_argument("--aox-trials", type=int, default=20)
+    ap.add_argument("--only-expand", action="store_true",
+                    help="time the expansion steps only (no e2e, planning metrics or CPU baseline)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -270,6 +272,17 @@ def main():
     planner.set_profiling(False)
     value, t_max, units = aggregate(R * args.steps, local_s)
     launches = sum(v["launches"] for v in kt.values())
+
+    if args.only_expand:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                              "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
+                              "kernel_ms_per_step": {k: v["ms"] / max(v["launches"], 1) for k, v in kt.items()},
+                              "gpu_launches": launches, "config": {"workload": WORKLOAD_DESC}}), flush=True)
+        planner.close()
+        if ws > 1:
+            dist.destroy_process_group()
+        return 0
 
     # ---- e2e through the C ABI: per-step info read back to the host ----
     e2e_times = []
