@@ -270,6 +270,42 @@ pakr_status pakr_kernel_times(pakr_planner *planner, double *ms_out, int64_t *la
 pakr_status pakr_philox4x32_10(pakr_planner *planner, const uint32_t *ctr, const uint32_t key[2], uint32_t *out,
                                int64_t n);
 
+/* Cost-pruned nearest neighbour that allocates no device memory.
+ *
+ * The paper has no counterpart of this call: it exists for callers that
+ * cannot allocate device memory where they need the search, such as code
+ * running while a stream is captured into a CUDA graph, real-time loops that
+ * forbid allocation after start-up, or plugins confined to another
+ * framework's memory pool.  It runs the same search kernel as pakr_expand's
+ * NearestNeighbor step, but its per-query scratch lives in one static device
+ * array built into the library (about 512 KB, held on every GPU that loads
+ * the library until the process exits) instead of planner memory.
+ *
+ * For each query i it writes nearest[i] = the index j < n with fcost[j] <
+ * bound that minimises the FP32 squared distance sum_k (queries[k*n_queries +
+ * i] - states[k*ld + j])^2, the lowest j on a tie, or -1 if no node is
+ * eligible; dist2[i] (optional) gets that squared distance (+inf if none).
+ *   states   device, d x ld floats, coordinate k of node j at states[k*ld + j]
+ *   ld, n    row stride and node count, 0 <= n <= ld < 2^31
+ *   d        3, 4, 5, 6 or 12
+ *   fcost    device, n floats (node j is eligible iff fcost[j] < bound)
+ *   queries  device, d x n_queries floats, coordinate k of query i at
+ *            queries[k*n_queries + i]
+ *   n_queries 0..65536; more is PAKR_ERR_INVALID_ARG (the static scratch limit)
+ *   nearest  device, n_queries int32; dist2 device, n_queries floats or NULL
+ *   cuda_stream  stream to enqueue on (NULL = default stream)
+ * Runs on the calling thread's current device and only enqueues work; no
+ * cudaMalloc, cudaFree or allocating library call is made.  The first call on
+ * a device looks up the scratch array's device address (and loads the
+ * library's GPU code if it is not loaded yet); make that first call before any
+ * stream capture.  All calls share the one scratch array and each clears what
+ * it uses, so calls whose kernels overlap on the GPU (different streams with
+ * no ordering between them) race and give wrong results; order them on one
+ * stream or with events. */
+pakr_status pakr_nearest_static(const float *states, int64_t ld, int64_t n, int32_t d, const float *fcost,
+                                float bound, const float *queries, int32_t n_queries, int32_t *nearest,
+                                float *dist2, void *cuda_stream);
+
 /* Library version string. */
 const char *pakr_version(void);
 

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libpakr.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["pakr_kernels.cu", "pakr_api.cu"]
+SOURCES = ["pakr_kernels.cu", "pakr_api.cu", "pakr_static.cu"]
 HEADERS = ["pakr_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]

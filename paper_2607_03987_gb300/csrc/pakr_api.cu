@@ -31,6 +31,13 @@ pakr_status fail(pakr_status st, const char *fmt, ...)
     return st;
 }
 
+}  // namespace
+
+// Error message sink shared with the other translation units of the library.
+void pakr::record_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
+namespace {
+
 #define CUDA_TRY(expr)                                                                                                 \
     do {                                                                                                               \
         cudaError_t e_ = (expr);                                                                                       \

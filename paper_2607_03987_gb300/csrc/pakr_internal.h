@@ -136,6 +136,9 @@ cudaError_t launch_plan_step(const DevProblem &P, Ctl *ctl, const DevTree &T, co
 cudaError_t launch_truncate(Ctl *ctl, int count, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int64_t n, cudaStream_t s);
 
+// Sets the calling thread's pakr_last_error() message (pakr_api.cu).
+void record_error(const char *msg);
+
 // Occupancy-derived sizes (pakr_kernels.cu).
 int nn_blocks_per_sm(int d, int variant);
 int prop_blocks_per_sm(int dyn, int threads, int smem);

@@ -81,7 +81,7 @@ class Path(C.Structure):
 EXPORTED = [
     "pakr_workspace_size", "pakr_create", "pakr_destroy", "pakr_last_error", "pakr_tree_reset",
     "pakr_expand", "pakr_plan", "pakr_tree_export", "pakr_tree_import", "pakr_tree_truncate", "pakr_debug_last_expand",
-    "pakr_set_profiling", "pakr_kernel_times", "pakr_philox4x32_10", "pakr_version",
+    "pakr_set_profiling", "pakr_kernel_times", "pakr_philox4x32_10", "pakr_nearest_static", "pakr_version",
 ]
 
 _lib = None
@@ -117,6 +117,8 @@ def lib():
     L.pakr_kernel_times.argtypes = [C.c_void_p, _PD, _PI64, C.POINTER(C.c_char_p), C.c_int32]
     L.pakr_philox4x32_10.argtypes = [C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                      C.POINTER(C.c_uint32), C.c_int64]
+    L.pakr_nearest_static.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p, C.c_float,
+                                      C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
     for name in EXPORTED:
         fn = getattr(L, name)
         if fn.restype is C.c_int or name in ("pakr_workspace_size",):
