@@ -79,7 +79,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
         except OSError:
@@ -162,6 +162,54 @@ def cpu_baseline(spec, tree, seed, target_s=10.0):
                       f"{N_PREFILL}-node tree ({rollouts} rollouts, {t1:.1f} s single-threaded FP64)"}
 
 
+
+def tree_size_sweep(dev, stream, steps=10, warmup=3):
+    """Expansions/s at fixed tree sizes: the paper's tier sizes 4^6..4^10 for the
+    3D double integrator, and up to 4,000,000 nodes for the 12D quadrotor
+    (4096 parents x 16 controls), each tree prefilled uniformly, L2 flushed
+    before every timed step."""
+    import torch
+
+    from paper_2607_03987_gb300 import pakr
+    from paper_2607_03987_gb300 import workloads as W
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    out = []
+    cases = [("di3", [4 ** 6, 4 ** 7, 4 ** 8, 4 ** 9, 4 ** 10 - 8192], {}),
+             ("quad12", [4 ** 6, 4 ** 8, 4 ** 10, 4_000_000 - 65536], {})]
+    for name, sizes, over in cases:
+        spec = W.problem(name, env_seed=0, **over)
+        tree = W.prefilled_tree(spec, max(sizes), seed=3)
+        planner = pakr.Planner(spec, device=dev, stream=stream)
+        planner.tree_import(tree, spec["x_goal"])
+        R = spec["K"] * spec["k"]
+        for n in sizes:
+            for w in range(warmup):
+                planner.tree_truncate(n)
+                planner.expand(np.inf, 900 + w, info=False)
+            planner.set_profiling(True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for s_, (a, b) in enumerate(ev):
+                planner.tree_truncate(n)
+                flush.zero_()
+                a.record(stream)
+                planner.expand(np.inf, s_, info=False)
+                b.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+            kt = planner.kernel_times()
+            planner.set_profiling(False)
+            nn_ms = kt["k_nn"]["ms"] / max(kt["k_nn"]["launches"], 1)
+            out.append({"workload": name, "n": n, "parents": spec["K"], "branching": spec["k"],
+                        "rollouts_per_s": R / (ms * 1e-3), "ms_per_step": ms,
+                        "nn_ms": nn_ms, "nn_tflops": nn_flops_per_launch(spec["K"], n, spec["d"]) / (nn_ms * 1e-3) / 1e12,
+                        "propagate_ms": kt["k_propagate"]["ms"] / max(kt["k_propagate"]["launches"], 1),
+                        "append_ms": kt["k_append"]["ms"] / max(kt["k_append"]["launches"], 1),
+                        "sample_ms": kt["k_sample"]["ms"] / max(kt["k_sample"]["launches"], 1)})
+        planner.close()
+        del tree
+    return out
+
 def run_reference(args):
     ws, rank, local = _dist_env()
     if rank != 0:
@@ -204,12 +252,13 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="pakr", choices=["pakr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ttfs-trials", type=int, default=100)
     ap.add_argument("--aox-trials", type=int, default=20)
+    ap.add_argument("--no-sweep", action="store_true", help="skip the tree-size sweep")
     ap.add_argument("--only-expand", action="store_true",
                     help="time the expansion steps only (no e2e, planning metrics or CPU baseline)")
     args = ap.parse_args()
@@ -242,6 +291,7 @@ def main():
     def one_step(seed, info=False):
         return planner.expand(np.inf, seed, info=info)
 
+    clocks = ClockSampler(dev).start()  # samples span the warm-up and the timed steps
     for w in range(args.warmup):
         planner.tree_truncate(N_PREFILL)
         one_step(10_000 + w)
@@ -251,7 +301,6 @@ def main():
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     planner.set_profiling(True)
-    clocks = ClockSampler(dev).start()
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -367,6 +416,8 @@ def main():
                                        "straight_line_lower_bound": float(np.linalg.norm(
                                            plan_spec["x_goal"][:3] - plan_spec["x_init"][:3]) - plan_spec["goal_r"])},
         }
+        if not args.no_sweep:
+            line["by_tree_size"] = tree_size_sweep(dev, stream)
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(spec, tree, seed=7)
         print(json.dumps(line), flush=True)

@@ -89,7 +89,7 @@ Layout make_layout(const DimInfo &di, int64_t cap, int K, int k, int nb, int ns,
         return at;
     };
     const size_t R = (size_t)K * k;
-    const size_t nblk = (R + kPropThreads - 1) / kPropThreads;
+    const size_t nblk = (R * 8 + kPropThreads - 1) / kPropThreads;  // blocks at the largest lane count
     const size_t c = (size_t)cap;
     L.X = take(sizeof(float) * di.d * c);
     L.U = take(sizeof(float) * di.m * c);
@@ -517,15 +517,23 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
     } else {
         C.nn_variant = 0;
         C.nn_threads = 64;
-        C.nn_qpt = 1;
+        C.nn_qpt = 2;
     }
     const int per_block = C.nn_threads * C.nn_qpt;
     C.nn_qgroups = (p->K + per_block - 1) / per_block;
     const int occ = std::max(1, nn_blocks_per_sm(di.d, C.nn_variant));
     C.nn_chunks = std::max(1, sms * occ / C.nn_qgroups);
     const int64_t R = (int64_t)p->K * p->k;
+    // Lanes per rollout: enough threads for about one resident wave on every
+    // SM, but no more lanes than there are obstacles to split between them.
+    const int n_obs = desc->n_boxes + desc->n_spheres;
+    int lanes = 1;
+    while (lanes < 8 && R * lanes * 2 <= (int64_t)sms * 1024 && lanes * 2 <= std::max(1, n_obs))
+        lanes *= 2;
+    C.prop_lanes = lanes;
     C.prop_threads = kPropThreads;
-    C.prop_blocks = (int)((R + kPropThreads - 1) / kPropThreads);
+    const int64_t rollouts_per_block = kPropThreads / lanes;
+    C.prop_blocks = (int)((R + rollouts_per_block - 1) / rollouts_per_block);
     C.obs_smem_bytes = (int)((2 * desc->n_boxes + desc->n_spheres) * sizeof(float4) + kMaxD * sizeof(float));
     *out = p;
     g_last_error.clear();

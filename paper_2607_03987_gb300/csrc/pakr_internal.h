@@ -110,9 +110,10 @@ struct DevPlanBufs {
 
 // Launch configuration chosen at create.
 struct LaunchCfg {
-    int nn_variant;     // 0: 64 threads x 1 query, 1: 128 x 2, 2: 256 x 4
+    int nn_variant;     // 0: 64 threads x 2 queries, 1: 128 x 2, 2: 256 x 4
     int nn_threads, nn_qpt, nn_qgroups, nn_chunks;
     int prop_threads, prop_blocks;
+    int prop_lanes;     // lanes per rollout in k_propagate (1, 2, 4 or 8); k_append takes prop_threads / prop_lanes
     int sample_threads, sample_blocks;
     int obs_smem_bytes; // shared memory for obstacles + goal
 };
@@ -141,6 +142,5 @@ void record_error(const char *msg);
 
 // Occupancy-derived sizes (pakr_kernels.cu).
 int nn_blocks_per_sm(int d, int variant);
-int prop_blocks_per_sm(int dyn, int threads, int smem);
 
 }  // namespace pakr

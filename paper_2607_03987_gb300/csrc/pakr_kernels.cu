@@ -309,42 +309,94 @@ __global__ void k_sample(DevProblem P, Ctl *ctl, DevWork W, float bound, unsigne
 // ---------------------------------------------------------------------------
 // k_nn: cost-pruned brute-force nearest neighbour.
 //
-// Block (chunk c, query group g): QPT queries per thread held in registers,
-// nodes [c*per, (c+1)*per) streamed as TILE-node tiles into shared memory,
-// node-major with rows padded to DP = 4*ceil(D/4) floats so each node is read
-// with DP/4 broadcast 128-bit loads.  Ineligible nodes (f-cost not below the
-// bound) and padding get +inf in coordinate 0, so their squared distance is
-// +inf and never wins the strict comparison.  Within a thread nodes are
-// visited in ascending index order, so a strict '<' keeps the lowest index;
-// across threads and chunks the packed key (distance bits << 32 | index) is
-// merged with atomicMin, which orders by distance and then by index
-// (distances are non-negative, so their IEEE bits order like the values).
+// Block (chunk c, query group g): 2*QP queries per thread in registers,
+// nodes [c*per, (c+1)*per) streamed in TILE-node tiles through shared memory.
+// A tile row holds the node's negated coordinates (scaled by the square roots
+// of the NN weights), so q - x is one FADD.  PACKED keeps the queries as QP
+// float2 pairs and duplicates each coordinate in the row, (-x0,-x0,-x1,...),
+// so one FADD2 / FFMA2 serves two queries; the scalar form keeps 2*QP queries
+// and single coordinates.  Packed and scalar IEEE operations round alike, so
+// both give the same distance bits.
+//
+// Ineligible nodes (f-cost not below the bound) and padding get +inf in
+// coordinate 0: their squared distance is +inf and never wins.  The argmin is
+// lazy: each group of G consecutive nodes yields a running minimum per query
+// (one FMNMX per pair); a strictly smaller group minimum replaces the best
+// distance and records that group.  After the chunk, each query recomputes
+// the distances of its best group from global memory with the same
+// operations and keeps the first node that reaches the best: nodes are
+// visited in ascending order and only a strictly smaller group minimum
+// replaces the best, so a tie resolves to the lowest index.  Across threads
+// and chunks the packed key (distance bits << 32 | index) is merged with
+// atomicMin, ordering by distance and then by index (non-negative floats
+// order like their IEEE bits).
 // ---------------------------------------------------------------------------
-template <int D, int QPT, int NT, int TILE>
-__global__ void __launch_bounds__(NT) k_nn(DevProblem P, const Ctl *__restrict__ ctl, DevTree T, DevWork W)
+// Resident blocks per SM the register budget is set for: about 80 registers
+// per thread for D <= 6, 128 for D = 12.
+template <int D, int NT>
+struct NnMinBlocks {
+    static constexpr int value = 65536 / (NT * (D <= 6 ? 80 : 128));
+};
+
+// First node of the group [j0, j0 + G) whose squared distance to the query
+// equals best; eligibility and arithmetic exactly as the tile staging and the
+// scan loop apply them.
+template <int D, int G>
+__device__ __forceinline__ int resolve_group(const DevProblem &P, const DevTree &T, int j0, int end, float bound,
+                                             const float *qv, float best)
 {
-    constexpr int DP = (D + 3) / 4 * 4;
-    constexpr int DV = DP / 4;
-    __shared__ __align__(16) float s_node[TILE * DP];
+    for (int g = 0; g < G; ++g) {
+        const int j = j0 + g;
+        if (j >= end)
+            break;
+        if (!(T.fcost[j] < bound))
+            continue;
+        float acc = 0.f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const float nx = -(T.X[(size_t)a * P.cap + j] * P.sw[a]);
+            const float diff = __fadd_rn(qv[a], nx);
+            acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
+        }
+        if (acc == best)
+            return j;
+    }
+    return j0;  // not reached: the group minimum came from one of its nodes
+}
+
+template <int D, int QP, int NT, int TILE, int G, bool PACKED>
+__global__ void __launch_bounds__(NT, (NnMinBlocks<D, NT>::value))
+    k_nn(DevProblem P, const Ctl *__restrict__ ctl, DevTree T, DevWork W)
+{
+    constexpr int NQ = 2 * QP;                                       // queries per thread
+    constexpr int RW = PACKED ? (2 * D + 3) / 4 * 4 : (D + 3) / 4 * 4;  // floats per tile row
+    constexpr int RV = RW / 4;
+    static_assert(TILE % G == 0, "tile must hold whole groups");
+    __shared__ __align__(16) float s_node[TILE * RW];
 
     const int n = ctl->n_start;
     const float bound = ctl->bound;
     const int K = P.K;
     const int cap = P.cap;
     const int tid = threadIdx.x;
-    const int qbase = blockIdx.y * NT * QPT;
+    const int qbase = blockIdx.y * NT * NQ;
+    const float inf = __int_as_float(0x7f800000);
 
-    float q[QPT][D];
-    float best[QPT];
-    int bidx[QPT];
+    // query qi of this thread is qbase + qi * NT + tid; packed pair p holds queries 2p and 2p+1
+    float qs[NQ][D];
 #pragma unroll
-    for (int qi = 0; qi < QPT; ++qi) {
+    for (int qi = 0; qi < NQ; ++qi) {
         const int qid = qbase + qi * NT + tid;
 #pragma unroll
         for (int a = 0; a < D; ++a)
-            q[qi][a] = (qid < K) ? W.xr[(size_t)a * K + qid] * P.sw[a] : 0.f;
-        best[qi] = __int_as_float(0x7f800000);
-        bidx[qi] = -1;
+            qs[qi][a] = (qid < K) ? W.xr[(size_t)a * K + qid] * P.sw[a] : 0.f;
+    }
+    float best[NQ];
+    int bgrp[NQ];
+#pragma unroll
+    for (int qi = 0; qi < NQ; ++qi) {
+        best[qi] = inf;
+        bgrp[qi] = -1;
     }
 
     const int nchunks = gridDim.x;
@@ -352,106 +404,145 @@ __global__ void __launch_bounds__(NT) k_nn(DevProblem P, const Ctl *__restrict__
     per = (per + TILE - 1) / TILE * TILE;
     const int start = blockIdx.x * per;
     const int end = min(n, start + per);
+    const float4 *s4 = reinterpret_cast<const float4 *>(s_node);
 
     for (int t0 = start; t0 < end; t0 += TILE) {
         __syncthreads();
         for (int e = tid; e < TILE; e += NT) {
             const int j = t0 + e;
-            float v[DP];
             const bool in = j < end;
             const bool ok = in && (T.fcost[j] < bound);
+            float row[RW];
 #pragma unroll
-            for (int a = 0; a < DP; ++a)
-                v[a] = (a < D && in) ? T.X[(size_t)a * cap + j] * P.sw[a] : 0.f;
-            if (!ok)
-                v[0] = __int_as_float(0x7f800000);
-            float4 *dst = reinterpret_cast<float4 *>(&s_node[e * DP]);
+            for (int a = 0; a < RW; ++a)
+                row[a] = 0.f;
 #pragma unroll
-            for (int c = 0; c < DV; ++c)
-                dst[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+            for (int a = 0; a < D; ++a) {
+                float v = in ? T.X[(size_t)a * cap + j] * P.sw[a] : 0.f;
+                if (a == 0 && !ok)
+                    v = inf;
+                if (PACKED) {
+                    row[2 * a] = -v;
+                    row[2 * a + 1] = -v;
+                } else {
+                    row[a] = -v;
+                }
+            }
+            float4 *dst = reinterpret_cast<float4 *>(&s_node[e * RW]);
+#pragma unroll
+            for (int c = 0; c < RV; ++c)
+                dst[c] = make_float4(row[4 * c], row[4 * c + 1], row[4 * c + 2], row[4 * c + 3]);
         }
         __syncthreads();
-        const float4 *s4 = reinterpret_cast<const float4 *>(s_node);
-#pragma unroll 2
-        for (int e = 0; e < TILE; ++e) {
-            float xn[DP];
+        for (int e0 = 0; e0 < TILE; e0 += G) {
+            float m[NQ];
 #pragma unroll
-            for (int c = 0; c < DV; ++c) {
-                const float4 t = s4[e * DV + c];
-                xn[4 * c] = t.x;
-                xn[4 * c + 1] = t.y;
-                xn[4 * c + 2] = t.z;
-                xn[4 * c + 3] = t.w;
+            for (int qi = 0; qi < NQ; ++qi)
+                m[qi] = inf;
+#pragma unroll 2
+            for (int g = 0; g < G; ++g) {
+                const float4 *src = s4 + (e0 + g) * RV;
+                float nx[RW];
+#pragma unroll
+                for (int c = 0; c < RV; ++c) {
+                    const float4 t = src[c];
+                    nx[4 * c] = t.x;
+                    nx[4 * c + 1] = t.y;
+                    nx[4 * c + 2] = t.z;
+                    nx[4 * c + 3] = t.w;
+                }
+                if (PACKED) {
+#pragma unroll
+                    for (int p = 0; p < QP; ++p) {
+                        float2 acc;
+#pragma unroll
+                        for (int a = 0; a < D; ++a) {
+                            const float2 diff = __fadd2_rn(make_float2(qs[2 * p][a], qs[2 * p + 1][a]),
+                                                           make_float2(nx[2 * a], nx[2 * a + 1]));
+                            acc = (a == 0) ? __fmul2_rn(diff, diff) : __ffma2_rn(diff, diff, acc);
+                        }
+                        m[2 * p] = fminf(m[2 * p], acc.x);
+                        m[2 * p + 1] = fminf(m[2 * p + 1], acc.y);
+                    }
+                } else {
+#pragma unroll
+                    for (int qi = 0; qi < NQ; ++qi) {
+                        float acc;
+#pragma unroll
+                        for (int a = 0; a < D; ++a) {
+                            const float diff = __fadd_rn(qs[qi][a], nx[a]);
+                            acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
+                        }
+                        m[qi] = fminf(m[qi], acc);
+                    }
+                }
             }
 #pragma unroll
-            for (int qi = 0; qi < QPT; ++qi) {
-                float diff = q[qi][0] - xn[0];
-                float acc = __fmul_rn(diff, diff);
-#pragma unroll
-                for (int a = 1; a < D; ++a) {
-                    diff = q[qi][a] - xn[a];
-                    acc = __fmaf_rn(diff, diff, acc);
-                }
-                if (acc < best[qi]) {
-                    best[qi] = acc;
-                    bidx[qi] = t0 + e;
-                }
+            for (int qi = 0; qi < NQ; ++qi) {
+                const bool better = m[qi] < best[qi];
+                best[qi] = better ? m[qi] : best[qi];
+                bgrp[qi] = better ? t0 + e0 : bgrp[qi];
             }
         }
     }
 #pragma unroll
-    for (int qi = 0; qi < QPT; ++qi) {
+    for (int qi = 0; qi < NQ; ++qi) {
         const int qid = qbase + qi * NT + tid;
-        if (qid < K && bidx[qi] >= 0) {
+        if (qid < K && bgrp[qi] >= 0) {
+            const int j = resolve_group<D, G>(P, T, bgrp[qi], end, bound, qs[qi], best[qi]);
             const unsigned long long key =
-                ((unsigned long long)__float_as_uint(best[qi]) << 32) | (unsigned long long)(uint32_t)bidx[qi];
+                ((unsigned long long)__float_as_uint(best[qi]) << 32) | (unsigned long long)(uint32_t)j;
             atomicMin(&W.nn_key[qid], key);
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// k_propagate: one thread per rollout r = i*k + j.
+// k_propagate: LG lanes per rollout r = i*k + j (LG divides 32).
+//
+// Every lane of a rollout's group samples the same control (counter-based
+// Philox) and integrates the same RK4 steps, so their states are identical;
+// the obstacle tests of each substep are split across the group's lanes and
+// combined with a warp ballot.  The substep loop runs to the warp's longest
+// rollout so that every lane reaches each ballot.  With path-length cost and
+// the position heuristic, f = g + h never decreases along an edge (h is
+// 1-Lipschitz in position), so a partial f at or above the bound already
+// decides the prune.
 // ---------------------------------------------------------------------------
-template <int DYN>
-__device__ __forceinline__ int rollout(const DevProblem &P, float *x, const float *u, int S, float &g, float bound,
-                                       float &f_out, const float4 *boxes, const float4 *spheres, const float *goal)
+template <int D, int PD>
+__device__ __forceinline__ bool in_state_box(const float *x, const DevProblem &P)
 {
-    constexpr int D = Dims<DYN>::D, PD = Dims<DYN>::PD;
-    // f = g + h is non-decreasing along an edge for path-length cost with the
-    // position heuristic (h is 1-Lipschitz in position), so a partial f at or
-    // above the bound already decides the prune.
-    const bool early = (P.cost == COST_PATH_LENGTH) && (P.heuristic == H_POSITION);
-    if (P.cost == COST_DURATION) {
-        g = g + (float)S * P.dt;
-        if (!(g < bound))
-            return OUT_PRUNED;  // h >= 0
-    }
-    for (int s = 1; s <= S; ++s) {
-        float xp[PD];
+    bool ok = true;
 #pragma unroll
-        for (int a = 0; a < PD; ++a)
-            xp[a] = x[a];
-        rk4_step<DYN>(x, u, P.dt, P);
-        if (P.cost == COST_PATH_LENGTH) {
-            float dd = 0.f;
-#pragma unroll
-            for (int a = 0; a < PD; ++a)
-                dd += (x[a] - xp[a]) * (x[a] - xp[a]);
-            g += sqrtf(dd);
-        }
-        if (!state_valid<D, PD>(x, P, boxes, P.n_boxes, spheres, P.n_spheres))
-            return OUT_COLLIDED;
-        if (early && !(g + heuristic<D, PD>(x, P, goal) < bound))
-            return OUT_PRUNED;
-    }
-    f_out = g + heuristic<D, PD>(x, P, goal);
-    if (!(f_out < bound))
-        return OUT_PRUNED;
-    return OUT_APPENDED;
+    for (int a = 0; a < D; ++a)
+        ok = ok && (x[a] >= P.x_lo[a]) && (x[a] <= P.x_hi[a]);
+    return ok;
 }
 
-template <int DYN>
+template <int PD>
+__device__ __forceinline__ bool hits_obstacle(const float *x, const float4 *boxes, int nb, const float4 *spheres,
+                                              int ns, int first, int stride)
+{
+    for (int b = first; b < nb; b += stride) {
+        const float4 lo = boxes[2 * b], hi = boxes[2 * b + 1];
+        bool inside = (x[0] >= lo.x) & (x[0] <= hi.x) & (x[1] >= lo.y) & (x[1] <= hi.y);
+        if (PD > 2)
+            inside = inside & (x[2] >= lo.z) & (x[2] <= hi.z);
+        if (inside)
+            return true;
+    }
+    for (int s = first; s < ns; s += stride) {
+        const float4 c = spheres[s];
+        float dd = (x[0] - c.x) * (x[0] - c.x) + (x[1] - c.y) * (x[1] - c.y);
+        if (PD > 2)
+            dd += (x[2] - c.z) * (x[2] - c.z);
+        if (dd <= c.w * c.w)
+            return true;
+    }
+    return false;
+}
+
+template <int DYN, int LG>
 __global__ void __launch_bounds__(256) k_propagate(DevProblem P, Ctl *ctl, DevTree T, DevWork W)
 {
     constexpr int D = Dims<DYN>::D, M = Dims<DYN>::M, PD = Dims<DYN>::PD;
@@ -468,67 +559,115 @@ __global__ void __launch_bounds__(256) k_propagate(DevProblem P, Ctl *ctl, DevTr
     __syncthreads();
 
     const int R = P.K * P.k;
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % LG;
+    const unsigned gmask = (LG == 32 ? 0xFFFFFFFFu : ((1u << LG) - 1u)) << (lane - sub);
+    const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) / LG);
+    const bool have = r < R;
+    const float bound = ctl->bound;
+    const bool early = (P.cost == COST_PATH_LENGTH) && (P.heuristic == H_POSITION);
+
     int out = -1;
-    if (r < R) {
+    bool alive = false;
+    float u[M];
+    float x[D];
+    float g = 0.f, f = 0.f;
+    int S = 0, par = -1;
+    if (have) {
         const int i = r / P.k;
         const int j = r - i * P.k;
         const uint32_t it = ctl->iteration;
         const unsigned long long seed = ctl->seed;
-        const float bound = ctl->bound;
         // SampleControls: words 0..M-1 the control, word M the duration.
-        float u[M];
-        int S;
-        {
-            constexpr int NB = (M + 1 + 3) / 4;
-            uint32_t words[4 * NB];
+        constexpr int NB = (M + 1 + 3) / 4;
+        uint32_t words[4 * NB];
 #pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                const Words4 w = philox(it, (uint32_t)i, (uint32_t)j, (uint32_t)b, (uint32_t)seed,
-                                        (uint32_t)(seed >> 32));
+        for (int b = 0; b < NB; ++b) {
+            const Words4 w = philox(it, (uint32_t)i, (uint32_t)j, (uint32_t)b, (uint32_t)seed, (uint32_t)(seed >> 32));
 #pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    words[4 * b + t] = w.w[t];
-            }
-#pragma unroll
-            for (int a = 0; a < M; ++a)
-                u[a] = lerp_box(P.u_lo[a], P.u_hi[a], words[a]);
-            const uint64_t span = (uint64_t)(P.s_max - P.s_min + 1);
-            S = P.s_min + (int)(((uint64_t)words[M] * span) >> 32);
+            for (int t = 0; t < 4; ++t)
+                words[4 * b + t] = w.w[t];
         }
 #pragma unroll
         for (int a = 0; a < M; ++a)
-            W.st_u[(size_t)a * R + r] = u[a];
-        W.st_steps[r] = S;
-
+            u[a] = lerp_box(P.u_lo[a], P.u_hi[a], words[a]);
+        const uint64_t span = (uint64_t)(P.s_max - P.s_min + 1);
+        S = P.s_min + (int)(((uint64_t)words[M] * span) >> 32);
         const unsigned long long key = W.nn_key[i];
         if (key == kNoKey) {
             out = OUT_NO_PARENT;
         } else {
-            const int par = (int)(uint32_t)(key & 0xFFFFFFFFull);
-            float x[D];
+            par = (int)(uint32_t)(key & 0xFFFFFFFFull);
 #pragma unroll
             for (int a = 0; a < D; ++a)
                 x[a] = T.X[(size_t)a * P.cap + par];
-            float g = T.cost[par];
-            float f = 0.f;
-            out = rollout<DYN>(P, x, u, S, g, bound, f, s_box, s_sph, s_goal);
-            if (out == OUT_APPENDED) {
-#pragma unroll
-                for (int a = 0; a < D; ++a)
-                    W.st_x[(size_t)a * R + r] = x[a];
-                W.st_cost[r] = g;
-                W.st_f[r] = f;
-                W.st_parent[r] = par;
-                W.goal[r] = in_goal<PD>(x, P, s_goal) ? 1 : 0;
+            g = T.cost[par];
+            alive = true;
+            if (P.cost == COST_DURATION) {
+                g = g + (float)S * P.dt;
+                if (!(g < bound)) {  // h >= 0
+                    out = OUT_PRUNED;
+                    alive = false;
+                }
             }
+        }
+    }
+    const int s_warp = __reduce_max_sync(0xFFFFFFFFu, alive ? S : 0);
+    for (int s = 1; s <= s_warp; ++s) {
+        const bool act = alive && s <= S;
+        bool inb = true;
+        if (act) {
+            float xp[PD];
+#pragma unroll
+            for (int a = 0; a < PD; ++a)
+                xp[a] = x[a];
+            rk4_step<DYN>(x, u, P.dt, P);
+            if (P.cost == COST_PATH_LENGTH) {
+                float dd = 0.f;
+#pragma unroll
+                for (int a = 0; a < PD; ++a)
+                    dd += (x[a] - xp[a]) * (x[a] - xp[a]);
+                g += sqrtf(dd);
+            }
+            inb = in_state_box<D, PD>(x, P);
+        }
+        const bool hit = act && inb && hits_obstacle<PD>(x, s_box, P.n_boxes, s_sph, P.n_spheres, sub, LG);
+        const unsigned any = __ballot_sync(0xFFFFFFFFu, hit);
+        if (act) {
+            if (!inb || (any & gmask)) {
+                out = OUT_COLLIDED;
+                alive = false;
+            } else if (early && !(g + heuristic<D, PD>(x, P, s_goal) < bound)) {
+                out = OUT_PRUNED;
+                alive = false;
+            }
+        }
+    }
+    if (alive) {
+        f = g + heuristic<D, PD>(x, P, s_goal);
+        out = (f < bound) ? OUT_APPENDED : OUT_PRUNED;
+    }
+    const bool leader = have && sub == 0;
+    if (leader) {
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+            W.st_u[(size_t)a * R + r] = u[a];
+        W.st_steps[r] = S;
+        if (out == OUT_APPENDED) {
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                W.st_x[(size_t)a * R + r] = x[a];
+            W.st_cost[r] = g;
+            W.st_f[r] = f;
+            W.st_parent[r] = par;
+            W.goal[r] = in_goal<PD>(x, P, s_goal) ? 1 : 0;
         }
         W.outcome[r] = (int8_t)out;
     }
-    const int n_cand = __syncthreads_count(out == OUT_APPENDED);
-    const int n_pr = __syncthreads_count(out == OUT_PRUNED);
-    const int n_col = __syncthreads_count(out == OUT_COLLIDED);
-    const int n_np = __syncthreads_count(out == OUT_NO_PARENT);
+    const int n_cand = __syncthreads_count(leader && out == OUT_APPENDED);
+    const int n_pr = __syncthreads_count(leader && out == OUT_PRUNED);
+    const int n_col = __syncthreads_count(leader && out == OUT_COLLIDED);
+    const int n_np = __syncthreads_count(leader && out == OUT_NO_PARENT);
     if (threadIdx.x == 0) {
         W.block_count[blockIdx.x] = n_cand;
         if (n_pr)
@@ -834,6 +973,8 @@ __global__ void k_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t
     }
 
 constexpr int kNnTile = 256;
+constexpr int kNnGroup = 8;
+constexpr bool kNnPacked = true;
 
 cudaError_t launch_sample(const DevProblem &P, Ctl *ctl, const DevWork &W, const LaunchCfg &L, float bound,
                           unsigned long long seed, int mode, cudaStream_t s)
@@ -849,9 +990,9 @@ static cudaError_t launch_nn_d(const DevProblem &P, const Ctl *ctl, const DevTre
 {
     const dim3 grid(L.nn_chunks, L.nn_qgroups);
     switch (L.nn_variant) {
-    case 0: k_nn<D, 1, 64, kNnTile><<<grid, 64, 0, s>>>(P, ctl, T, W); break;
-    case 1: k_nn<D, 2, 128, kNnTile><<<grid, 128, 0, s>>>(P, ctl, T, W); break;
-    default: k_nn<D, 4, 256, kNnTile><<<grid, 256, 0, s>>>(P, ctl, T, W); break;
+    case 0: k_nn<D, 1, 64, kNnTile, kNnGroup, kNnPacked><<<grid, 64, 0, s>>>(P, ctl, T, W); break;
+    case 1: k_nn<D, 1, 128, kNnTile, kNnGroup, kNnPacked><<<grid, 128, 0, s>>>(P, ctl, T, W); break;
+    default: k_nn<D, 2, 256, kNnTile, kNnGroup, kNnPacked><<<grid, 256, 0, s>>>(P, ctl, T, W); break;
     }
     return cudaGetLastError();
 }
@@ -863,18 +1004,32 @@ cudaError_t launch_nn(const DevProblem &P, const Ctl *ctl, const DevTree &T, con
     return cudaSuccess;
 }
 
+template <int DYN>
+static cudaError_t launch_propagate_dyn(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W,
+                                        const LaunchCfg &L, cudaStream_t s)
+{
+    switch (L.prop_lanes) {
+    case 1: k_propagate<DYN, 1><<<L.prop_blocks, L.prop_threads, L.obs_smem_bytes, s>>>(P, ctl, T, W); break;
+    case 2: k_propagate<DYN, 2><<<L.prop_blocks, L.prop_threads, L.obs_smem_bytes, s>>>(P, ctl, T, W); break;
+    case 4: k_propagate<DYN, 4><<<L.prop_blocks, L.prop_threads, L.obs_smem_bytes, s>>>(P, ctl, T, W); break;
+    case 8: k_propagate<DYN, 8><<<L.prop_blocks, L.prop_threads, L.obs_smem_bytes, s>>>(P, ctl, T, W); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_propagate(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
                              cudaStream_t s)
 {
-    PAKR_DISPATCH_DYN(P.dyn, (k_propagate<DYN_><<<L.prop_blocks, L.prop_threads, L.obs_smem_bytes, s>>>(
-                                 P, ctl, T, W)));
-    return cudaGetLastError();
+    PAKR_DISPATCH_DYN(P.dyn, return launch_propagate_dyn<DYN_>(P, ctl, T, W, L, s));
+    return cudaSuccess;
 }
 
 cudaError_t launch_append(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
                           cudaStream_t s)
 {
-    PAKR_DISPATCH_DYN(P.dyn, (k_append<Dims<DYN_>::D, Dims<DYN_>::M><<<L.prop_blocks, L.prop_threads, 0, s>>>(
+    const int rollouts_per_block = L.prop_threads / L.prop_lanes;
+    PAKR_DISPATCH_DYN(P.dyn, (k_append<Dims<DYN_>::D, Dims<DYN_>::M><<<L.prop_blocks, rollouts_per_block, 0, s>>>(
                                  P, ctl, T, W, L.prop_blocks)));
     return cudaGetLastError();
 }
@@ -927,9 +1082,9 @@ static int nn_occ(int variant)
 {
     int nb = 0;
     switch (variant) {
-    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nn<D, 1, 64, kNnTile>, 64, 0); break;
-    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nn<D, 2, 128, kNnTile>, 128, 0); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nn<D, 4, 256, kNnTile>, 256, 0); break;
+    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nn<D, 1, 64, kNnTile, kNnGroup, kNnPacked>, 64, 0); break;
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nn<D, 1, 128, kNnTile, kNnGroup, kNnPacked>, 128, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nn<D, 2, 256, kNnTile, kNnGroup, kNnPacked>, 256, 0); break;
     }
     return nb;
 }
@@ -944,21 +1099,6 @@ int nn_blocks_per_sm(int d, int variant)
     case 12: return nn_occ<12>(variant);
     default: return 0;
     }
-}
-
-int prop_blocks_per_sm(int dyn, int threads, int smem)
-{
-    int nb = 0;
-    switch (dyn) {
-    case DI2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<DI2>, threads, smem); break;
-    case DI3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<DI3>, threads, smem); break;
-    case QUAD12: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<QUAD12>, threads, smem); break;
-    case DUBINS3D: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<DUBINS3D>, threads, smem); break;
-    case UNICYCLE1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<UNICYCLE1>, threads, smem); break;
-    case UNICYCLE2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<UNICYCLE2>, threads, smem); break;
-    default: break;
-    }
-    return nb;
 }
 
 }  // namespace pakr

@@ -165,7 +165,7 @@ extern "C" pakr_status pakr_nearest_static(const float *states, int64_t ld, int6
     } else {
         L.nn_variant = 0;
         L.nn_threads = 64;
-        L.nn_qpt = 1;
+        L.nn_qpt = 2;
     }
     {
         std::lock_guard<std::mutex> lock(g_setup_mu);
