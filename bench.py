@@ -183,7 +183,7 @@ def tree_size_sweep(dev, stream, steps=10, warmup=3):
         planner = pakr.Planner(spec, device=dev, stream=stream)
         planner.tree_import(tree, spec["x_goal"])
         R = spec["K"] * spec["k"]
-        for n in sizes:
+        for n in sorted(sizes, reverse=True):  # truncation only shrinks the tree: largest size first
             for w in range(warmup):
                 planner.tree_truncate(n)
                 planner.expand(np.inf, 900 + w, info=False)
@@ -207,6 +207,7 @@ def tree_size_sweep(dev, stream, steps=10, warmup=3):
                         "append_ms": kt["k_append"]["ms"] / max(kt["k_append"]["launches"], 1),
                         "sample_ms": kt["k_sample"]["ms"] / max(kt["k_sample"]["launches"], 1)})
         planner.close()
+        out.sort(key=lambda r: (r["workload"], r["n"]))
         del tree
     return out
 

@@ -12,7 +12,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libpakr.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["pakr_kernels.cu", "pakr_api.cu", "pakr_static.cu"]
-HEADERS = ["pakr_internal.h"]
+HEADERS = ["pakr_internal.h", "pakr_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -1,705 +1,58 @@
 // pakr_kernels.cu -- sm_103a kernels of one PAKR expansion iteration
-// (Algorithm 1 inner loop) and of the device-resident AO-x loop.
+// (Algorithm 1 inner loop) and of the device-resident AO-x loop.  The block
+// bodies live in pakr_device.cuh.
 //
 //   k_sample     SampleStates: Philox4x32-10 uniform states, clears the NN keys,
 //                snapshots the tree size (the frozen snapshot of Sec. IV-B).
-//   k_nn         NearestNeighbor among nodes with f-cost below the bound:
-//                queries in registers, FP32 SoA tree tiles staged through shared
-//                memory, lexicographic (distance, index) minimum merged across
-//                node chunks with one 64-bit atomicMin per query and chunk.
+//   k_nn         NearestNeighbor among nodes with f-cost below the bound.
 //   k_propagate  SampleControls + RK4 Propagate + per-substep validity +
-//                cost-bounded pruning + goal test, one thread per rollout,
-//                obstacles staged in shared memory.
-//   k_append     insert survivors in ascending rollout order (block counts +
-//                warp-ballot ranks), truncate at the cap, cheapest goal child.
+//                cost-bounded pruning + goal test.
+//   k_append     insert survivors in ascending rollout order, truncate at the
+//                cap, cheapest goal child.
 //   k_plan_*     AO-x bookkeeping inside a conditional-while CUDA graph.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
-#include "pakr_internal.h"
+#include "pakr_device.cuh"
 
 namespace pakr {
 
 // ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
-// 32x32 -> 64-bit products, Weyl key schedule.
-// ---------------------------------------------------------------------------
-struct Words4 {
-    uint32_t w[4];
-};
-
-__device__ __forceinline__ Words4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
-                                         uint32_t k1)
-{
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        if (round) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-        const uint32_t n0 = hi1 ^ c1 ^ k0;
-        const uint32_t n2 = hi0 ^ c3 ^ k1;
-        c0 = n0;
-        c1 = lo1;
-        c2 = n2;
-        c3 = lo0;
-    }
-    Words4 r;
-    r.w[0] = c0;
-    r.w[1] = c1;
-    r.w[2] = c2;
-    r.w[3] = c3;
-    return r;
-}
-
-// Top 24 bits as a uniform in [0, 1): exact in FP32.
-__device__ __forceinline__ float u01(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
-
-__device__ __forceinline__ float lerp_box(float lo, float hi, uint32_t w) { return __fmaf_rn(hi - lo, u01(w), lo); }
-
-__device__ __forceinline__ unsigned long long globaltimer_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// ---------------------------------------------------------------------------
-// Dynamics x' = f(x, u) (Eq. 1) per model, FP32.
-// ---------------------------------------------------------------------------
-template <int DYN> struct Dims;
-template <> struct Dims<DI2> { static constexpr int D = 4, M = 2, PD = 2; };
-template <> struct Dims<DI3> { static constexpr int D = 6, M = 3, PD = 3; };
-template <> struct Dims<QUAD12> { static constexpr int D = 12, M = 4, PD = 3; };
-template <> struct Dims<DUBINS3D> { static constexpr int D = 6, M = 3, PD = 3; };
-template <> struct Dims<UNICYCLE1> { static constexpr int D = 3, M = 2, PD = 2; };
-template <> struct Dims<UNICYCLE2> { static constexpr int D = 5, M = 2, PD = 2; };
-
-template <int DYN>
-__device__ __forceinline__ void deriv(const float *x, const float *u, float *xd, const DevProblem &P);
-
-// Double integrator: position' = velocity, velocity' = control.
-template <>
-__device__ __forceinline__ void deriv<DI2>(const float *x, const float *u, float *xd, const DevProblem &)
-{
-    xd[0] = x[2];
-    xd[1] = x[3];
-    xd[2] = u[0];
-    xd[3] = u[1];
-}
-
-template <>
-__device__ __forceinline__ void deriv<DI3>(const float *x, const float *u, float *xd, const DevProblem &)
-{
-    xd[0] = x[3];
-    xd[1] = x[4];
-    xd[2] = x[5];
-    xd[3] = u[0];
-    xd[4] = u[1];
-    xd[5] = u[2];
-}
-
-// Quadcopter, Z-Y-X Euler angles, body-frame linear / angular velocity, thrust
-// along body z, gravity -g along world z: p' = R v, eta' = W(eta) omega,
-// v' = v x omega + R^T g + T/m e3, omega' = I^-1 (tau - omega x I omega).
-template <>
-__device__ __forceinline__ void deriv<QUAD12>(const float *x, const float *u, float *xd, const DevProblem &P)
-{
-    const float mass = P.model[0], Ixx = P.model[1], Iyy = P.model[2], Izz = P.model[3], g = P.model[4];
-    float sf, cf, st, ct, sp, cp;
-    sincosf(x[3], &sf, &cf);
-    sincosf(x[4], &st, &ct);
-    sincosf(x[5], &sp, &cp);
-    const float r00 = cp * ct, r01 = cp * st * sf - sp * cf, r02 = cp * st * cf + sp * sf;
-    const float r10 = sp * ct, r11 = sp * st * sf + cp * cf, r12 = sp * st * cf - cp * sf;
-    const float r20 = -st, r21 = ct * sf, r22 = ct * cf;
-    const float vu = x[6], vv = x[7], vw = x[8];
-    const float wp = x[9], wq = x[10], wr = x[11];
-    xd[0] = r00 * vu + r01 * vv + r02 * vw;
-    xd[1] = r10 * vu + r11 * vv + r12 * vw;
-    xd[2] = r20 * vu + r21 * vv + r22 * vw;
-    const float tt = st / ct;
-    xd[3] = wp + sf * tt * wq + cf * tt * wr;
-    xd[4] = cf * wq - sf * wr;
-    xd[5] = (sf * wq + cf * wr) / ct;
-    xd[6] = (vv * wr - vw * wq) + (-g * r20);
-    xd[7] = (vw * wp - vu * wr) + (-g * r21);
-    xd[8] = (vu * wq - vv * wp) + (-g * r22) + u[0] / mass;
-    const float Ip = Ixx * wp, Iq = Iyy * wq, Ir = Izz * wr;
-    xd[9] = (u[1] - (wq * Ir - wr * Iq)) / Ixx;
-    xd[10] = (u[2] - (wr * Ip - wp * Ir)) / Iyy;
-    xd[11] = (u[3] - (wp * Iq - wq * Ip)) / Izz;
-}
-
-// Dubins airplane: speed v along the heading given by yaw and pitch.
-template <>
-__device__ __forceinline__ void deriv<DUBINS3D>(const float *x, const float *u, float *xd, const DevProblem &)
-{
-    float sy, cy, sp, cp;
-    sincosf(x[3], &sy, &cy);
-    sincosf(x[4], &sp, &cp);
-    xd[0] = x[5] * cp * cy;
-    xd[1] = x[5] * cp * sy;
-    xd[2] = x[5] * sp;
-    xd[3] = u[0];
-    xd[4] = u[1];
-    xd[5] = u[2];
-}
-
-template <>
-__device__ __forceinline__ void deriv<UNICYCLE1>(const float *x, const float *u, float *xd, const DevProblem &)
-{
-    float s, c;
-    sincosf(x[2], &s, &c);
-    xd[0] = u[0] * c;
-    xd[1] = u[0] * s;
-    xd[2] = u[1];
-}
-
-template <>
-__device__ __forceinline__ void deriv<UNICYCLE2>(const float *x, const float *u, float *xd, const DevProblem &)
-{
-    float s, c;
-    sincosf(x[2], &s, &c);
-    xd[0] = x[3] * c;
-    xd[1] = x[3] * s;
-    xd[2] = x[4];
-    xd[3] = u[0];
-    xd[4] = u[1];
-}
-
-// Classical RK4 step with the control held (Sec. IV-A).  The stage sum is
-// accumulated in the order k1 + 2 k2 + 2 k3 + k4.
-template <int DYN>
-__device__ __forceinline__ void rk4_step(float *x, const float *u, float h, const DevProblem &P)
-{
-    constexpr int D = Dims<DYN>::D;
-    float k[D], t[D], acc[D];
-    deriv<DYN>(x, u, k, P);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        acc[a] = k[a];
-        t[a] = x[a] + 0.5f * h * k[a];
-    }
-    deriv<DYN>(t, u, k, P);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        acc[a] = acc[a] + 2.0f * k[a];
-        t[a] = x[a] + 0.5f * h * k[a];
-    }
-    deriv<DYN>(t, u, k, P);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        acc[a] = acc[a] + 2.0f * k[a];
-        t[a] = x[a] + h * k[a];
-    }
-    deriv<DYN>(t, u, k, P);
-    const float h6 = h / 6.0f;
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-        x[a] = x[a] + h6 * (acc[a] + k[a]);
-}
-
-// ---------------------------------------------------------------------------
-// Validity (point robot): closed state box is valid, closed boxes and balls
-// are obstacles.  Obstacles come as padded float4 records.
-// ---------------------------------------------------------------------------
-template <int D, int PD>
-__device__ __forceinline__ bool state_valid(const float *x, const DevProblem &P, const float4 *boxes, int nb,
-                                            const float4 *spheres, int ns)
-{
-    bool ok = true;
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-        ok = ok && (x[a] >= P.x_lo[a]) && (x[a] <= P.x_hi[a]);
-    if (!ok)
-        return false;
-    for (int b = 0; b < nb; ++b) {
-        const float4 lo = boxes[2 * b], hi = boxes[2 * b + 1];
-        bool inside = (x[0] >= lo.x) & (x[0] <= hi.x) & (x[1] >= lo.y) & (x[1] <= hi.y);
-        if (PD > 2)
-            inside = inside & (x[2] >= lo.z) & (x[2] <= hi.z);
-        if (inside)
-            return false;
-    }
-    for (int s = 0; s < ns; ++s) {
-        const float4 c = spheres[s];
-        float dd = (x[0] - c.x) * (x[0] - c.x) + (x[1] - c.y) * (x[1] - c.y);
-        if (PD > 2)
-            dd += (x[2] - c.z) * (x[2] - c.z);
-        if (dd <= c.w * c.w)
-            return false;
-    }
-    return true;
-}
-
-// h of the f-cost (Sec. IV): distance of the position to the goal ball
-// (duration cost: divided by the speed bound), or the whole-state Euclidean
-// distance to the goal state when the full-state formula is selected.
-template <int D, int PD>
-__device__ __forceinline__ float heuristic(const float *x, const DevProblem &P, const float *goal)
-{
-    if (P.heuristic == H_FULLSTATE) {
-        float dd = 0.f;
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-            dd += (x[a] - goal[a]) * (x[a] - goal[a]);
-        return sqrtf(dd);
-    }
-    float dd = 0.f;
-#pragma unroll
-    for (int a = 0; a < PD; ++a)
-        dd += (x[a] - goal[a]) * (x[a] - goal[a]);
-    const float h = fmaxf(0.f, sqrtf(dd) - P.goal_r);
-    if (P.cost == COST_DURATION)
-        return P.h_speed > 0.f ? h / P.h_speed : 0.f;
-    return h;
-}
-
-template <int PD>
-__device__ __forceinline__ bool in_goal(const float *x, const DevProblem &P, const float *goal)
-{
-    float dd = 0.f;
-#pragma unroll
-    for (int a = 0; a < PD; ++a)
-        dd += (x[a] - goal[a]) * (x[a] - goal[a]);
-    return dd <= P.goal_r * P.goal_r;
-}
-
-// ---------------------------------------------------------------------------
-// k_sample: SampleStates and per-batch reset of the control block.
+// Expansion kernels.
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void k_sample(DevProblem P, Ctl *ctl, DevWork W, float bound, unsigned long long seed_arg, int mode)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long seed = (mode == MODE_EXPAND) ? seed_arg : ctl->seed;
-    const uint32_t it = ctl->iteration;
-    if (i < P.K) {
-        constexpr int NB = (D + 3) / 4;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const Words4 w = philox(it, (uint32_t)i, 0xFFFFFFFFu, (uint32_t)b, (uint32_t)seed, (uint32_t)(seed >> 32));
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int dim = 4 * b + t;
-                if (dim < D)
-                    W.xr[(size_t)dim * P.K + i] = lerp_box(P.x_lo[dim], P.x_hi[dim], w.w[t]);
-            }
-        }
-        W.nn_key[i] = kNoKey;
-    }
+    if (i < P.K)
+        sample_state<D>(P, W, i, ctl->iteration, seed);
     if (i == 0) {
-        ctl->bound = (mode == MODE_EXPAND) ? bound : ctl->c_best;
         if (mode == MODE_EXPAND)
             ctl->seed = seed_arg;
-        ctl->n_start = ctl->count;
-        ctl->goal_key = kNoKey;
-        ctl->n_appended = 0;
-        ctl->n_pruned = 0;
-        ctl->n_collided = 0;
-        ctl->n_no_parent = 0;
-        ctl->n_dropped = 0;
+        begin_batch(ctl, (mode == MODE_EXPAND) ? bound : ctl->c_best);
     }
-}
-
-// ---------------------------------------------------------------------------
-// k_nn: cost-pruned brute-force nearest neighbour.
-//
-// Block (chunk c, query group g): 2*QP queries per thread in registers,
-// nodes [c*per, (c+1)*per) streamed in TILE-node tiles through shared memory.
-// A tile row holds the node's negated coordinates (scaled by the square roots
-// of the NN weights), so q - x is one FADD.  PACKED keeps the queries as QP
-// float2 pairs and duplicates each coordinate in the row, (-x0,-x0,-x1,...),
-// so one FADD2 / FFMA2 serves two queries; the scalar form keeps 2*QP queries
-// and single coordinates.  Packed and scalar IEEE operations round alike, so
-// both give the same distance bits.
-//
-// Ineligible nodes (f-cost not below the bound) and padding get +inf in
-// coordinate 0: their squared distance is +inf and never wins.  The argmin is
-// lazy: each group of G consecutive nodes yields a running minimum per query
-// (one FMNMX per pair); a strictly smaller group minimum replaces the best
-// distance and records that group.  After the chunk, each query recomputes
-// the distances of its best group from global memory with the same
-// operations and keeps the first node that reaches the best: nodes are
-// visited in ascending order and only a strictly smaller group minimum
-// replaces the best, so a tie resolves to the lowest index.  Across threads
-// and chunks the packed key (distance bits << 32 | index) is merged with
-// atomicMin, ordering by distance and then by index (non-negative floats
-// order like their IEEE bits).
-// ---------------------------------------------------------------------------
-// Resident blocks per SM the register budget is set for: about 80 registers
-// per thread for D <= 6, 128 for D = 12.
-template <int D, int NT>
-struct NnMinBlocks {
-    static constexpr int value = 65536 / (NT * (D <= 6 ? 80 : 128));
-};
-
-// First node of the group [j0, j0 + G) whose squared distance to the query
-// equals best; eligibility and arithmetic exactly as the tile staging and the
-// scan loop apply them.
-template <int D, int G>
-__device__ __forceinline__ int resolve_group(const DevProblem &P, const DevTree &T, int j0, int end, float bound,
-                                             const float *qv, float best)
-{
-    for (int g = 0; g < G; ++g) {
-        const int j = j0 + g;
-        if (j >= end)
-            break;
-        if (!(T.fcost[j] < bound))
-            continue;
-        float acc = 0.f;
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            const float nx = -(T.X[(size_t)a * P.cap + j] * P.sw[a]);
-            const float diff = __fadd_rn(qv[a], nx);
-            acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
-        }
-        if (acc == best)
-            return j;
-    }
-    return j0;  // not reached: the group minimum came from one of its nodes
 }
 
 template <int D, int QP, int NT, int TILE, int G, bool PACKED>
 __global__ void __launch_bounds__(NT, (NnMinBlocks<D, NT>::value))
     k_nn(DevProblem P, const Ctl *__restrict__ ctl, DevTree T, DevWork W)
 {
-    constexpr int NQ = 2 * QP;                                       // queries per thread
-    constexpr int RW = PACKED ? (2 * D + 3) / 4 * 4 : (D + 3) / 4 * 4;  // floats per tile row
-    constexpr int RV = RW / 4;
-    static_assert(TILE % G == 0, "tile must hold whole groups");
+    constexpr int RW = PACKED ? (2 * D + 3) / 4 * 4 : (D + 3) / 4 * 4;
     __shared__ __align__(16) float s_node[TILE * RW];
-
     const int n = ctl->n_start;
-    const float bound = ctl->bound;
-    const int K = P.K;
-    const int cap = P.cap;
-    const int tid = threadIdx.x;
-    const int qbase = blockIdx.y * NT * NQ;
-    const float inf = __int_as_float(0x7f800000);
-
-    // query qi of this thread is qbase + qi * NT + tid; packed pair p holds queries 2p and 2p+1
-    float qs[NQ][D];
-#pragma unroll
-    for (int qi = 0; qi < NQ; ++qi) {
-        const int qid = qbase + qi * NT + tid;
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-            qs[qi][a] = (qid < K) ? W.xr[(size_t)a * K + qid] * P.sw[a] : 0.f;
-    }
-    float best[NQ];
-    int bgrp[NQ];
-#pragma unroll
-    for (int qi = 0; qi < NQ; ++qi) {
-        best[qi] = inf;
-        bgrp[qi] = -1;
-    }
-
-    const int nchunks = gridDim.x;
-    int per = (n + nchunks - 1) / nchunks;
-    per = (per + TILE - 1) / TILE * TILE;
+    const int per = nn_chunk_nodes<G>(n, gridDim.x);
     const int start = blockIdx.x * per;
     const int end = min(n, start + per);
-    const float4 *s4 = reinterpret_cast<const float4 *>(s_node);
-
-    for (int t0 = start; t0 < end; t0 += TILE) {
-        __syncthreads();
-        for (int e = tid; e < TILE; e += NT) {
-            const int j = t0 + e;
-            const bool in = j < end;
-            const bool ok = in && (T.fcost[j] < bound);
-            float row[RW];
-#pragma unroll
-            for (int a = 0; a < RW; ++a)
-                row[a] = 0.f;
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                float v = in ? T.X[(size_t)a * cap + j] * P.sw[a] : 0.f;
-                if (a == 0 && !ok)
-                    v = inf;
-                if (PACKED) {
-                    row[2 * a] = -v;
-                    row[2 * a + 1] = -v;
-                } else {
-                    row[a] = -v;
-                }
-            }
-            float4 *dst = reinterpret_cast<float4 *>(&s_node[e * RW]);
-#pragma unroll
-            for (int c = 0; c < RV; ++c)
-                dst[c] = make_float4(row[4 * c], row[4 * c + 1], row[4 * c + 2], row[4 * c + 3]);
-        }
-        __syncthreads();
-        for (int e0 = 0; e0 < TILE; e0 += G) {
-            float m[NQ];
-#pragma unroll
-            for (int qi = 0; qi < NQ; ++qi)
-                m[qi] = inf;
-#pragma unroll 2
-            for (int g = 0; g < G; ++g) {
-                const float4 *src = s4 + (e0 + g) * RV;
-                float nx[RW];
-#pragma unroll
-                for (int c = 0; c < RV; ++c) {
-                    const float4 t = src[c];
-                    nx[4 * c] = t.x;
-                    nx[4 * c + 1] = t.y;
-                    nx[4 * c + 2] = t.z;
-                    nx[4 * c + 3] = t.w;
-                }
-                if (PACKED) {
-#pragma unroll
-                    for (int p = 0; p < QP; ++p) {
-                        float2 acc;
-#pragma unroll
-                        for (int a = 0; a < D; ++a) {
-                            const float2 diff = __fadd2_rn(make_float2(qs[2 * p][a], qs[2 * p + 1][a]),
-                                                           make_float2(nx[2 * a], nx[2 * a + 1]));
-                            acc = (a == 0) ? __fmul2_rn(diff, diff) : __ffma2_rn(diff, diff, acc);
-                        }
-                        m[2 * p] = fminf(m[2 * p], acc.x);
-                        m[2 * p + 1] = fminf(m[2 * p + 1], acc.y);
-                    }
-                } else {
-#pragma unroll
-                    for (int qi = 0; qi < NQ; ++qi) {
-                        float acc;
-#pragma unroll
-                        for (int a = 0; a < D; ++a) {
-                            const float diff = __fadd_rn(qs[qi][a], nx[a]);
-                            acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
-                        }
-                        m[qi] = fminf(m[qi], acc);
-                    }
-                }
-            }
-#pragma unroll
-            for (int qi = 0; qi < NQ; ++qi) {
-                const bool better = m[qi] < best[qi];
-                best[qi] = better ? m[qi] : best[qi];
-                bgrp[qi] = better ? t0 + e0 : bgrp[qi];
-            }
-        }
-    }
-#pragma unroll
-    for (int qi = 0; qi < NQ; ++qi) {
-        const int qid = qbase + qi * NT + tid;
-        if (qid < K && bgrp[qi] >= 0) {
-            const int j = resolve_group<D, G>(P, T, bgrp[qi], end, bound, qs[qi], best[qi]);
-            const unsigned long long key =
-                ((unsigned long long)__float_as_uint(best[qi]) << 32) | (unsigned long long)(uint32_t)j;
-            atomicMin(&W.nn_key[qid], key);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// k_propagate: LG lanes per rollout r = i*k + j (LG divides 32).
-//
-// Every lane of a rollout's group samples the same control (counter-based
-// Philox) and integrates the same RK4 steps, so their states are identical;
-// the obstacle tests of each substep are split across the group's lanes and
-// combined with a warp ballot.  The substep loop runs to the warp's longest
-// rollout so that every lane reaches each ballot.  With path-length cost and
-// the position heuristic, f = g + h never decreases along an edge (h is
-// 1-Lipschitz in position), so a partial f at or above the bound already
-// decides the prune.
-// ---------------------------------------------------------------------------
-template <int D, int PD>
-__device__ __forceinline__ bool in_state_box(const float *x, const DevProblem &P)
-{
-    bool ok = true;
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-        ok = ok && (x[a] >= P.x_lo[a]) && (x[a] <= P.x_hi[a]);
-    return ok;
-}
-
-template <int PD>
-__device__ __forceinline__ bool hits_obstacle(const float *x, const float4 *boxes, int nb, const float4 *spheres,
-                                              int ns, int first, int stride)
-{
-    for (int b = first; b < nb; b += stride) {
-        const float4 lo = boxes[2 * b], hi = boxes[2 * b + 1];
-        bool inside = (x[0] >= lo.x) & (x[0] <= hi.x) & (x[1] >= lo.y) & (x[1] <= hi.y);
-        if (PD > 2)
-            inside = inside & (x[2] >= lo.z) & (x[2] <= hi.z);
-        if (inside)
-            return true;
-    }
-    for (int s = first; s < ns; s += stride) {
-        const float4 c = spheres[s];
-        float dd = (x[0] - c.x) * (x[0] - c.x) + (x[1] - c.y) * (x[1] - c.y);
-        if (PD > 2)
-            dd += (x[2] - c.z) * (x[2] - c.z);
-        if (dd <= c.w * c.w)
-            return true;
-    }
-    return false;
+    nn_scan<D, QP, NT, TILE, G, PACKED>(P, T, W, ctl->bound, blockIdx.y * NT * 2 * QP, start, end, s_node);
 }
 
 template <int DYN, int LG>
 __global__ void __launch_bounds__(256) k_propagate(DevProblem P, Ctl *ctl, DevTree T, DevWork W)
 {
-    constexpr int D = Dims<DYN>::D, M = Dims<DYN>::M, PD = Dims<DYN>::PD;
     extern __shared__ float4 s_obs[];
-    float4 *s_box = s_obs;
-    float4 *s_sph = s_obs + 2 * P.n_boxes;
-    float *s_goal = reinterpret_cast<float *>(s_sph + P.n_spheres);
-    for (int t = threadIdx.x; t < 2 * P.n_boxes; t += blockDim.x)
-        s_box[t] = P.boxes[t];
-    for (int t = threadIdx.x; t < P.n_spheres; t += blockDim.x)
-        s_sph[t] = P.spheres[t];
-    if (threadIdx.x < D)
-        s_goal[threadIdx.x] = ctl->x_goal[threadIdx.x];
-    __syncthreads();
-
-    const int R = P.K * P.k;
-    const int lane = threadIdx.x & 31;
-    const int sub = lane % LG;
-    const unsigned gmask = (LG == 32 ? 0xFFFFFFFFu : ((1u << LG) - 1u)) << (lane - sub);
-    const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) / LG);
-    const bool have = r < R;
-    const float bound = ctl->bound;
-    const bool early = (P.cost == COST_PATH_LENGTH) && (P.heuristic == H_POSITION);
-
-    int out = -1;
-    bool alive = false;
-    float u[M];
-    float x[D];
-    float g = 0.f, f = 0.f;
-    int S = 0, par = -1;
-    if (have) {
-        const int i = r / P.k;
-        const int j = r - i * P.k;
-        const uint32_t it = ctl->iteration;
-        const unsigned long long seed = ctl->seed;
-        // SampleControls: words 0..M-1 the control, word M the duration.
-        constexpr int NB = (M + 1 + 3) / 4;
-        uint32_t words[4 * NB];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const Words4 w = philox(it, (uint32_t)i, (uint32_t)j, (uint32_t)b, (uint32_t)seed, (uint32_t)(seed >> 32));
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-                words[4 * b + t] = w.w[t];
-        }
-#pragma unroll
-        for (int a = 0; a < M; ++a)
-            u[a] = lerp_box(P.u_lo[a], P.u_hi[a], words[a]);
-        const uint64_t span = (uint64_t)(P.s_max - P.s_min + 1);
-        S = P.s_min + (int)(((uint64_t)words[M] * span) >> 32);
-        const unsigned long long key = W.nn_key[i];
-        if (key == kNoKey) {
-            out = OUT_NO_PARENT;
-        } else {
-            par = (int)(uint32_t)(key & 0xFFFFFFFFull);
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-                x[a] = T.X[(size_t)a * P.cap + par];
-            g = T.cost[par];
-            alive = true;
-            if (P.cost == COST_DURATION) {
-                g = g + (float)S * P.dt;
-                if (!(g < bound)) {  // h >= 0
-                    out = OUT_PRUNED;
-                    alive = false;
-                }
-            }
-        }
-    }
-    const int s_warp = __reduce_max_sync(0xFFFFFFFFu, alive ? S : 0);
-    for (int s = 1; s <= s_warp; ++s) {
-        const bool act = alive && s <= S;
-        bool inb = true;
-        if (act) {
-            float xp[PD];
-#pragma unroll
-            for (int a = 0; a < PD; ++a)
-                xp[a] = x[a];
-            rk4_step<DYN>(x, u, P.dt, P);
-            if (P.cost == COST_PATH_LENGTH) {
-                float dd = 0.f;
-#pragma unroll
-                for (int a = 0; a < PD; ++a)
-                    dd += (x[a] - xp[a]) * (x[a] - xp[a]);
-                g += sqrtf(dd);
-            }
-            inb = in_state_box<D, PD>(x, P);
-        }
-        const bool hit = act && inb && hits_obstacle<PD>(x, s_box, P.n_boxes, s_sph, P.n_spheres, sub, LG);
-        const unsigned any = __ballot_sync(0xFFFFFFFFu, hit);
-        if (act) {
-            if (!inb || (any & gmask)) {
-                out = OUT_COLLIDED;
-                alive = false;
-            } else if (early && !(g + heuristic<D, PD>(x, P, s_goal) < bound)) {
-                out = OUT_PRUNED;
-                alive = false;
-            }
-        }
-    }
-    if (alive) {
-        f = g + heuristic<D, PD>(x, P, s_goal);
-        out = (f < bound) ? OUT_APPENDED : OUT_PRUNED;
-    }
-    const bool leader = have && sub == 0;
-    if (leader) {
-#pragma unroll
-        for (int a = 0; a < M; ++a)
-            W.st_u[(size_t)a * R + r] = u[a];
-        W.st_steps[r] = S;
-        if (out == OUT_APPENDED) {
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-                W.st_x[(size_t)a * R + r] = x[a];
-            W.st_cost[r] = g;
-            W.st_f[r] = f;
-            W.st_parent[r] = par;
-            W.goal[r] = in_goal<PD>(x, P, s_goal) ? 1 : 0;
-        }
-        W.outcome[r] = (int8_t)out;
-    }
-    const int n_cand = __syncthreads_count(leader && out == OUT_APPENDED);
-    const int n_pr = __syncthreads_count(leader && out == OUT_PRUNED);
-    const int n_col = __syncthreads_count(leader && out == OUT_COLLIDED);
-    const int n_np = __syncthreads_count(leader && out == OUT_NO_PARENT);
-    if (threadIdx.x == 0) {
-        W.block_count[blockIdx.x] = n_cand;
-        if (n_pr)
-            atomicAdd(&ctl->n_pruned, n_pr);
-        if (n_col)
-            atomicAdd(&ctl->n_collided, n_col);
-        if (n_np)
-            atomicAdd(&ctl->n_no_parent, n_np);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// k_append: survivors of block b go to n_start + (survivors of blocks < b) +
-// (rank inside the block), i.e. ascending rollout order; positions at or past
-// the cap are dropped.  Goal children compete through atomicMin on the packed
-// (cost bits << 32 | node) key: the cheapest wins, the lowest node on a tie.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int block_sum(int v, int *s_tmp)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0)
-        s_tmp[wid] = v;
-    __syncthreads();
-    int tot = 0;
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int w = 0; w < nw; ++w)
-        tot += s_tmp[w];
-    return tot;
+    propagate_block<DYN, LG>(P, ctl, T, W, blockIdx.x, s_obs);
 }
 
 template <int D, int M>
@@ -707,60 +60,7 @@ __global__ void __launch_bounds__(256) k_append(DevProblem P, Ctl *ctl, DevTree 
 {
     __shared__ int s_tmp[32];
     __shared__ int s_warp[32];
-    const int R = P.K * P.k;
-    int part = 0, tot = 0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-        const int c = W.block_count[b];
-        tot += c;
-        if (b < (int)blockIdx.x)
-            part += c;
-    }
-    part = block_sum(part, s_tmp);
-    tot = block_sum(tot, s_tmp);
-
-    const int n_start = ctl->n_start;
-    const int cap = P.cap;
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool cand = (r < R) && (W.outcome[r] == OUT_APPENDED);
-    const unsigned bal = __ballot_sync(0xFFFFFFFFu, cand);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0)
-        s_warp[wid] = __popc(bal);
-    __syncthreads();
-    int warp_off = 0;
-    for (int w = 0; w < wid; ++w)
-        warp_off += s_warp[w];
-    const long long pos = (long long)n_start + part + warp_off + __popc(bal & ((1u << lane) - 1u));
-    if (cand) {
-        if (pos < cap) {
-            const int p = (int)pos;
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-                T.X[(size_t)a * cap + p] = W.st_x[(size_t)a * R + r];
-#pragma unroll
-            for (int a = 0; a < M; ++a)
-                T.U[(size_t)a * cap + p] = W.st_u[(size_t)a * R + r];
-            const float c = W.st_cost[r];
-            T.cost[p] = c;
-            T.fcost[p] = W.st_f[r];
-            T.parent[p] = W.st_parent[r];
-            T.steps[p] = W.st_steps[r];
-            if (W.goal[r])
-                atomicMin(&ctl->goal_key, ((unsigned long long)__float_as_uint(c) << 32) | (unsigned long long)p);
-        } else {
-            W.outcome[r] = OUT_DROPPED;
-        }
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        long long room = (long long)cap - n_start;
-        if (room < 0)
-            room = 0;
-        const int app = (int)min((long long)tot, room);
-        ctl->n_appended = app;
-        ctl->n_dropped = tot - app;
-        ctl->count = n_start + app;
-        ctl->iteration = ctl->iteration + 1u;
-    }
+    append_block<D, M>(P, ctl, T, W, blockIdx.x, nblk, blockDim.x, s_tmp, s_warp);
 }
 
 // ---------------------------------------------------------------------------
@@ -860,85 +160,10 @@ __global__ void k_plan_step(DevProblem P, Ctl *ctl, DevTree T, const PlanParams 
 {
     __shared__ int s_len;
     __shared__ int s_found;
-    const int lane = threadIdx.x;
-    if (lane == 0) {
-        const unsigned long long now = globaltimer_ns();
-        ctl->iterations_done += 1;
-        const unsigned long long key = ctl->goal_key;
-        s_found = 0;
-        s_len = 0;
-        if (key != kNoKey) {
-            const float c = __uint_as_float((uint32_t)(key >> 32));
-            const int node = (int)(uint32_t)(key & 0xFFFFFFFFull);
-            ctl->c_best = c;
-            const int ns = ctl->n_solutions;
-            if (ns < B.hist_cap) {
-                B.hist_t[ns] = now - ctl->t0_ns;
-                B.hist_cost[ns] = c;
-                B.hist_iter[ns] = ctl->iterations_done - 1;
-            }
-            if (ns == 0)
-                ctl->t_first_ns = now - ctl->t0_ns;
-            ctl->n_solutions = ns + 1;
-            // ExtractPath: length first, bounded by the node count.
-            int len = 0;
-            const int limit = ctl->count + 1;
-            for (int v = node; v >= 0 && len <= limit; v = T.parent[v])
-                ++len;
-            if (len > limit) {
-                ctl->err |= ERR_PATH_CYCLE;
-                ctl->path_len = 0;
-            } else if (len > B.path_cap + 1) {
-                ctl->path_len = -len;
-            } else {
-                int at = len - 1;
-                for (int v = node; v >= 0; v = T.parent[v])
-                    B.path_nodes[at--] = v;
-                ctl->path_len = len;
-                s_len = len;
-            }
-            s_found = 1;
-        }
-    }
-    __syncwarp();
-    const int len = s_len;
-    for (int t = lane; t < len; t += 32) {
-        const int v = B.path_nodes[t];
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-            B.path_x[(size_t)t * D + a] = T.X[(size_t)a * P.cap + v];
-#pragma unroll
-        for (int a = 0; a < M; ++a)
-            B.path_u[(size_t)t * M + a] = T.U[(size_t)a * P.cap + v];
-        B.path_steps[t] = T.steps[v];
-    }
-    __syncwarp();
-    if (lane == 0) {
-        const unsigned long long now = globaltimer_ns();
-        bool stop = false;
-        bool restart = false;
-        if (s_found) {
-            restart = true;
-            if (pp->stop_at_first) {
-                stop = true;
-                ctl->plan_status = 1;
-            }
-        } else if (ctl->count >= P.cap) {
-            restart = true;
-            ctl->n_restarts += 1;
-        }
-        if (!s_found && ctl->n_no_parent >= P.K * P.k) {
-            stop = true;
-            ctl->plan_status = 3;
-        }
-        if (now - ctl->t0_ns >= pp->budget_ns || ctl->iterations_done >= pp->max_iterations)
-            stop = true;
-        if (restart)
-            ctl->count = 1;
-        ctl->plan_stop = stop ? 1 : 0;
-        ctl->t_end_ns = now;
+    const bool stop = aox_step_warp<D, M>(P, ctl, T, B, pp->stop_at_first, pp->budget_ns, pp->max_iterations, &s_len,
+                                          &s_found);
+    if (threadIdx.x == 0)
         cudaGraphSetConditional(h, stop ? 0u : 1u);
-    }
 }
 
 __global__ void k_truncate(Ctl *ctl, int count)
