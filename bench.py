@@ -211,6 +211,55 @@ def tree_size_sweep(dev, stream, steps=10, warmup=3):
         del tree
     return out
 
+
+def batched_vs_sequential(dev, stream, n_queries=256, seed=4242, max_iterations=2000, budget_s=20.0):
+    """Queries solved per second: 256 independent 3D double-integrator queries
+    (obstacles U{10..200}, tree caps U[64k, 1M], random start / goal pairs),
+    each planned to its first solution, as one autotuned persistent launch
+    (pakr_batch_plan under a CUDA graph) vs one pakr_plan call per query."""
+    import torch
+
+    from paper_2607_03987_gb300 import pakr
+    from paper_2607_03987_gb300 import workloads as W
+
+    base, queries = W.batch_queries(n_queries, env_seed=0)
+    bp = pakr.BatchPlanner(base, queries, device=dev, stream=stream)
+    tuning = bp.autotune(iterations=3, seed=1)
+    bp.plan(budget_s=budget_s, max_iterations=max_iterations, seed=seed + 1, stop_at_first=True)  # warm-up
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    rb = bp.plan(budget_s=budget_s, max_iterations=max_iterations, seed=seed, stop_at_first=True)
+    t_batch = time.perf_counter() - t0
+    bp.close()
+    planners = []
+    for q in queries:
+        spec = W.with_sizes(base, boxes=q["boxes"], spheres=q["spheres"], cap=q["cap"], x_init=q["x_init"],
+                            x_goal=q["x_goal"])
+        pl = pakr.Planner(spec, device=dev, stream=stream)
+        pl.plan(q["x_init"], q["x_goal"], budget_s=budget_s, max_iterations=2, seed=1)  # builds the graph
+        planners.append(pl)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    rs = [pl.plan(q["x_init"], q["x_goal"], budget_s=budget_s, max_iterations=max_iterations, seed=seed + i,
+                  stop_at_first=True) for i, (pl, q) in enumerate(zip(planners, queries))]
+    t_seq = time.perf_counter() - t0
+    for pl in planners:
+        pl.close()
+    solved_b = sum(1 for r in rb if r["n_solutions"] > 0)
+    solved_s = sum(1 for r in rs if r["n_solutions"] > 0)
+    same = all(a["iterations"] == b["iterations"] and (a["cost"] == b["cost"] or (a["n_solutions"] == 0 and
+                                                                                b["n_solutions"] == 0))
+               for a, b in zip(rb, rs))
+    iters = [r["iterations"] for r in rb]
+    return {"queries": n_queries, "batched_queries_per_s": n_queries / t_batch,
+            "sequential_queries_per_s": n_queries / t_seq, "speedup": t_seq / t_batch,
+            "batched_s": t_batch, "sequential_s": t_seq, "solved_batched": solved_b, "solved_sequential": solved_s,
+            "identical_results": bool(same), "iterations_p50": float(np.median(iters)),
+            "iterations_max": int(max(iters)), "tuning": tuning,
+            "workload": "256 x 3D double integrator, K=1024 x k=8 per query, obstacles U{10..200}, caps "
+                        "U[64k,1M], random start/goal pairs, plan to first solution; host wall clock including "
+                        "launch and result read-back"}
+
 def run_reference(args):
     ws, rank, local = _dist_env()
     if rank != 0:
@@ -260,6 +309,7 @@ def main():
     ap.add_argument("--ttfs-trials", type=int, default=100)
     ap.add_argument("--aox-trials", type=int, default=20)
     ap.add_argument("--no-sweep", action="store_true", help="skip the tree-size sweep")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-sequential comparison")
     ap.add_argument("--only-expand", action="store_true",
                     help="time the expansion steps only (no e2e, planning metrics or CPU baseline)")
     args = ap.parse_args()
@@ -419,6 +469,8 @@ def main():
         }
         if not args.no_sweep:
             line["by_tree_size"] = tree_size_sweep(dev, stream)
+        if not args.no_batched:
+            line["batched_256"] = batched_vs_sequential(dev, stream)
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(spec, tree, seed=7)
         print(json.dumps(line), flush=True)

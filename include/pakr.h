@@ -270,6 +270,78 @@ pakr_status pakr_kernel_times(pakr_planner *planner, double *ms_out, int64_t *la
 pakr_status pakr_philox4x32_10(pakr_planner *planner, const uint32_t *ctr, const uint32_t key[2], uint32_t *out,
                                int64_t n);
 
+/* ---------------------------------------------------------------------------
+ * Batched planning: many independent queries, one persistent launch.
+ *
+ * Each query is a full Algorithm 1 run (its own tree, c_best and AO-x state)
+ * with its own start, goal, obstacles and tree cap; dynamics, bounds, step,
+ * durations, goal radius, cost, heuristic, K and A are shared.  One
+ * cooperative kernel runs every query's expansions phase by phase
+ * (SampleStates, NearestNeighbor, Propagate, insert, AO-x step) with
+ * grid-wide barriers in between, spreading each phase's work items over all
+ * SMs; the launch is captured once into a CUDA graph.  Query q seeds its
+ * Philox stream with seed + q.
+ * ------------------------------------------------------------------------- */
+typedef struct pakr_batch pakr_batch;
+
+typedef struct pakr_batch_query {
+    const float *x_init;        /* d */
+    const float *x_goal;        /* d */
+    int32_t n_boxes;
+    const float *boxes;         /* n_boxes x (lo[p], hi[p]) */
+    int32_t n_spheres;
+    const float *spheres;       /* n_spheres x (c[p], r) */
+    int64_t tree_cap;           /* >= 1, <= 2^31 - 1 */
+} pakr_batch_query;
+
+/* Launch shape of the persistent kernel: threads per block (128 or 256; a
+ * nearest-neighbour work item covers 4 x block_threads queries) and tree
+ * nodes per nearest-neighbour work item (a multiple of 8, >= 64). */
+typedef struct pakr_batch_tuning {
+    int32_t block_threads;
+    int32_t nn_chunk;
+    /* outputs of pakr_batch_autotune */
+    int32_t n_tried;
+    double best_ms;             /* time of the chosen shape on the tuning run */
+} pakr_batch_tuning;
+
+typedef struct pakr_batch_result {
+    int32_t status;             /* PAKR_GOAL_REACHED, PAKR_BUDGET_EXPIRED, PAKR_NO_ELIGIBLE or PAKR_ERR_INVALID_ARG (bad start) */
+    int32_t n_solutions;
+    float cost;                 /* best cost, +inf if none */
+    int32_t n_edges;            /* edges of the best path (-1 if it exceeded path_cap) */
+    int64_t iterations;         /* expansion iterations of this query */
+    double t_first_solution_s;  /* device time to the first solution, < 0 if none */
+    int32_t n_restarts;
+    int32_t reserved;
+} pakr_batch_result;
+
+/* base: the shared problem (its obstacles and tree_cap are ignored; path_cap
+ * bounds each query's stored best path, 0 = 1024).  queries: n_queries
+ * entries, copied.  Allocates device memory for every query's tree. */
+pakr_status pakr_batch_create(const pakr_problem_desc *base, const pakr_batch_query *queries, int32_t n_queries,
+                              pakr_batch **out);
+void pakr_batch_destroy(pakr_batch *batch);
+
+/* Run every query's AO-x loop (as pakr_plan, flags PAKR_PLAN_STOP_AT_FIRST
+ * allowed) in one graph launch; results holds n_queries entries.
+ * Synchronises the stream.  Returns PAKR_OK when the launch completed. */
+pakr_status pakr_batch_plan(pakr_batch *batch, double budget_s, int64_t max_iterations, uint64_t seed, uint32_t flags,
+                            pakr_batch_result *results);
+
+/* Best path of query q after pakr_batch_plan (rows as in pakr_path). */
+pakr_status pakr_batch_path(pakr_batch *batch, int32_t query, float *states, float *controls, int32_t *steps,
+                            int32_t max_edges);
+
+/* Launch-shape autotuner: times pakr_batch_plan with every candidate shape
+ * (block_threads in {128, 256} x nn_chunk in {512, 1024, 2048, 4096, 8192})
+ * for `iterations` expansion iterations per query without stopping at
+ * solutions, keeps the fastest, and reports it. */
+pakr_status pakr_batch_autotune(pakr_batch *batch, int64_t iterations, uint64_t seed, pakr_batch_tuning *out);
+
+/* Set the launch shape directly (for example, a cached autotuner result). */
+pakr_status pakr_batch_set_tuning(pakr_batch *batch, const pakr_batch_tuning *tuning);
+
 /* Cost-pruned nearest neighbour that allocates no device memory.
  *
  * The paper has no counterpart of this call: it exists for callers that

@@ -11,10 +11,14 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libpakr.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["pakr_kernels.cu", "pakr_api.cu", "pakr_static.cu"]
+SOURCES = ["pakr_kernels.cu", "pakr_api.cu", "pakr_static.cu", "pakr_batch.cu"]
 HEADERS = ["pakr_internal.h", "pakr_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+# -fmad=false: no implicit multiply-add contraction, so every kernel that runs a
+# device function rounds it the same way whatever its template parameters (the
+# batched and single-query planners give bit-identical plans); the fused
+# multiply-adds that matter are written out as intrinsics.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
 
 def _nvcc():

@@ -350,6 +350,55 @@ pakr_status read_ctl(pakr_planner *p)
 
 }  // namespace
 
+// Checks the problem part of a description (everything but obstacles and
+// tree size) and fills the matching kernel constants; obstacles, counts and
+// the tree capacity are left for the caller.  Shared with the batched planner.
+pakr_status pakr::fill_problem(const pakr_problem_desc *desc, DevProblem *P, int *d_out, int *m_out, int *pdim_out)
+{
+    if (!desc || !P)
+        return fail(PAKR_ERR_INVALID_ARG, "NULL argument");
+    pakr_problem_desc d = *desc;
+    d.n_boxes = 0;
+    d.boxes = nullptr;
+    d.n_spheres = 0;
+    d.spheres = nullptr;
+    d.tree_cap = 1;
+    DimInfo di;
+    pakr_status st = check_desc(&d, &di);
+    if (st != PAKR_OK)
+        return st;
+    *P = DevProblem{};
+    P->dyn = d.dynamics;
+    P->d = di.d;
+    P->m = di.m;
+    P->pdim = di.pdim;
+    for (int a = 0; a < kMaxD; ++a) {
+        P->x_lo[a] = a < di.d ? d.x_lo[a] : 0.f;
+        P->x_hi[a] = a < di.d ? d.x_hi[a] : 0.f;
+        P->sw[a] = (a < di.d && d.nn_weights) ? std::sqrt(d.nn_weights[a]) : 1.f;
+    }
+    for (int a = 0; a < kMaxM; ++a) {
+        P->u_lo[a] = a < di.m ? d.u_lo[a] : 0.f;
+        P->u_hi[a] = a < di.m ? d.u_hi[a] : 0.f;
+    }
+    const float quad_default[5] = {1.f, 0.01f, 0.01f, 0.02f, 9.81f};
+    for (int a = 0; a < 8; ++a)
+        P->model[a] = a < 5 ? (d.model_params ? d.model_params[a] : quad_default[a]) : 0.f;
+    P->dt = d.dt;
+    P->goal_r = d.goal_radius;
+    P->h_speed = d.heuristic_speed;
+    P->s_min = d.steps_min;
+    P->s_max = d.steps_max;
+    P->cost = d.cost;
+    P->heuristic = d.heuristic;
+    P->K = d.n_parents;
+    P->k = d.branching;
+    *d_out = di.d;
+    *m_out = di.m;
+    *pdim_out = di.pdim;
+    return PAKR_OK;
+}
+
 extern "C" {
 
 const char *pakr_version(void) { return "pakr-gb300 0.1 (sm_103a)"; }

@@ -165,35 +165,37 @@ __device__ __forceinline__ void deriv<UNICYCLE2>(const float *x, const float *u,
 }
 
 // Classical RK4 step with the control held (Sec. IV-A).  The stage sum is
-// accumulated in the order k1 + 2 k2 + 2 k3 + k4.
+// accumulated in the order k1 + 2 k2 + 2 k3 + k4; the stage points and the
+// update are explicit fused multiply-adds.
 template <int DYN>
 __device__ __forceinline__ void rk4_step(float *x, const float *u, float h, const DevProblem &P)
 {
     constexpr int D = Dims<DYN>::D;
     float k[D], t[D], acc[D];
+    const float hh = 0.5f * h;
     deriv<DYN>(x, u, k, P);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         acc[a] = k[a];
-        t[a] = x[a] + 0.5f * h * k[a];
+        t[a] = __fmaf_rn(hh, k[a], x[a]);
     }
     deriv<DYN>(t, u, k, P);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        acc[a] = acc[a] + 2.0f * k[a];
-        t[a] = x[a] + 0.5f * h * k[a];
+        acc[a] = __fmaf_rn(2.0f, k[a], acc[a]);
+        t[a] = __fmaf_rn(hh, k[a], x[a]);
     }
     deriv<DYN>(t, u, k, P);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        acc[a] = acc[a] + 2.0f * k[a];
-        t[a] = x[a] + h * k[a];
+        acc[a] = __fmaf_rn(2.0f, k[a], acc[a]);
+        t[a] = __fmaf_rn(h, k[a], x[a]);
     }
     deriv<DYN>(t, u, k, P);
     const float h6 = h / 6.0f;
 #pragma unroll
     for (int a = 0; a < D; ++a)
-        x[a] = x[a] + h6 * (acc[a] + k[a]);
+        x[a] = __fmaf_rn(h6, acc[a] + k[a], x[a]);
 }
 
 // ---------------------------------------------------------------------------
@@ -856,6 +858,51 @@ __device__ __forceinline__ bool aox_step_warp(const DevProblem &P, Ctl *ctl, con
     }
     __syncwarp();
     return stop;
+}
+
+// Fresh AO-x run for one tree (Algorithm 1): the goal, the root
+// {(x_init, -, 0)}, c_best = +inf, the expansion counter at 0 and the device
+// clock started.  One thread.  Returns whether the loop should run (a valid
+// start, a positive budget and iteration cap).
+template <int DYN>
+__device__ __forceinline__ bool aox_init_one(const DevProblem &P, Ctl *ctl, const DevTree &T, const float *x_init,
+                                             const float *x_goal, unsigned long long seed, long long max_iterations,
+                                             unsigned long long budget_ns)
+{
+    constexpr int D = Dims<DYN>::D, M = Dims<DYN>::M, PD = Dims<DYN>::PD;
+    float x[D], goal[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        x[a] = x_init[a];
+        goal[a] = x_goal[a];
+        ctl->x_goal[a] = goal[a];
+        T.X[(size_t)a * P.cap] = x[a];
+    }
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+        T.U[(size_t)a * P.cap] = 0.f;
+    T.cost[0] = 0.f;
+    T.fcost[0] = heuristic<D, PD>(x, P, goal);
+    T.parent[0] = -1;
+    T.steps[0] = 0;
+    ctl->count = 1;
+    ctl->iteration = 0u;
+    ctl->seed = seed;
+    ctl->c_best = __int_as_float(0x7f800000);
+    ctl->iterations_done = 0;
+    ctl->n_solutions = 0;
+    ctl->n_restarts = 0;
+    ctl->path_len = 0;
+    ctl->err = 0;
+    ctl->t_first_ns = ~0ull;
+    const bool valid = state_valid<D, PD>(x, P, P.boxes, P.n_boxes, P.spheres, P.n_spheres);
+    ctl->plan_status = valid ? 0 : -1;
+    const bool run = valid && max_iterations > 0 && budget_ns > 0;
+    ctl->plan_stop = run ? 0 : 1;
+    const unsigned long long now = globaltimer_ns();
+    ctl->t0_ns = now;
+    ctl->t_end_ns = now;
+    return run;
 }
 
 }  // namespace pakr

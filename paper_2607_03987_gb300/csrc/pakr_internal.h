@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/pakr.h"
+
 namespace pakr {
 
 constexpr int kMaxD = 16;
@@ -139,6 +141,10 @@ cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_
 
 // Sets the calling thread's pakr_last_error() message (pakr_api.cu).
 void record_error(const char *msg);
+
+// Validates the problem part of a description (not obstacles or tree size)
+// and fills the kernel constants (pakr_api.cu).
+pakr_status fill_problem(const pakr_problem_desc *desc, DevProblem *P, int *d, int *m, int *pdim);
 
 // Occupancy-derived sizes (pakr_kernels.cu).
 int nn_blocks_per_sm(int d, int variant);

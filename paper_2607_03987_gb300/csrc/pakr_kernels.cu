@@ -113,41 +113,10 @@ __global__ void k_import_fcost(DevProblem P, Ctl *ctl, DevTree T, int count)
 template <int DYN>
 __global__ void k_plan_init(DevProblem P, Ctl *ctl, DevTree T, const PlanParams *pp, cudaGraphConditionalHandle h)
 {
-    constexpr int D = Dims<DYN>::D, M = Dims<DYN>::M, PD = Dims<DYN>::PD;
     if (threadIdx.x != 0 || blockIdx.x != 0)
         return;
-    float x[D], goal[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        x[a] = pp->x_init[a];
-        goal[a] = pp->x_goal[a];
-        ctl->x_goal[a] = goal[a];
-        T.X[(size_t)a * P.cap] = x[a];
-    }
-#pragma unroll
-    for (int a = 0; a < M; ++a)
-        T.U[(size_t)a * P.cap] = 0.f;
-    T.cost[0] = 0.f;
-    T.fcost[0] = heuristic<D, PD>(x, P, goal);
-    T.parent[0] = -1;
-    T.steps[0] = 0;
-    ctl->count = 1;
-    ctl->iteration = 0u;
-    ctl->seed = pp->seed;
-    ctl->c_best = __int_as_float(0x7f800000);
-    ctl->iterations_done = 0;
-    ctl->n_solutions = 0;
-    ctl->n_restarts = 0;
-    ctl->path_len = 0;
-    ctl->err = 0;
-    ctl->t_first_ns = ~0ull;
-    const bool valid = state_valid<D, PD>(x, P, P.boxes, P.n_boxes, P.spheres, P.n_spheres);
-    ctl->plan_status = valid ? 0 : -1;
-    const bool run = valid && pp->max_iterations > 0 && pp->budget_ns > 0;
-    ctl->plan_stop = run ? 0 : 1;
-    const unsigned long long now = globaltimer_ns();
-    ctl->t0_ns = now;
-    ctl->t_end_ns = now;
+    const bool run =
+        aox_init_one<DYN>(P, ctl, T, pp->x_init, pp->x_goal, pp->seed, pp->max_iterations, pp->budget_ns);
     cudaGraphSetConditional(h, run ? 1u : 0u);
 }
 

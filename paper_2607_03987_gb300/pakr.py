@@ -78,10 +78,32 @@ class Path(C.Structure):
     ]
 
 
+class BatchQuery(C.Structure):
+    _fields_ = [
+        ("x_init", _PF), ("x_goal", _PF), ("n_boxes", C.c_int32), ("boxes", _PF),
+        ("n_spheres", C.c_int32), ("spheres", _PF), ("tree_cap", C.c_int64),
+    ]
+
+
+class BatchTuning(C.Structure):
+    _fields_ = [("block_threads", C.c_int32), ("nn_chunk", C.c_int32), ("n_tried", C.c_int32),
+                ("best_ms", C.c_double)]
+
+
+class BatchResult(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32), ("n_solutions", C.c_int32), ("cost", C.c_float), ("n_edges", C.c_int32),
+        ("iterations", C.c_int64), ("t_first_solution_s", C.c_double), ("n_restarts", C.c_int32),
+        ("reserved", C.c_int32),
+    ]
+
+
 EXPORTED = [
     "pakr_workspace_size", "pakr_create", "pakr_destroy", "pakr_last_error", "pakr_tree_reset",
     "pakr_expand", "pakr_plan", "pakr_tree_export", "pakr_tree_import", "pakr_tree_truncate", "pakr_debug_last_expand",
     "pakr_set_profiling", "pakr_kernel_times", "pakr_philox4x32_10", "pakr_nearest_static", "pakr_version",
+    "pakr_batch_create", "pakr_batch_destroy", "pakr_batch_plan", "pakr_batch_path", "pakr_batch_autotune",
+    "pakr_batch_set_tuning",
 ]
 
 _lib = None
@@ -119,9 +141,16 @@ def lib():
                                      C.POINTER(C.c_uint32), C.c_int64]
     L.pakr_nearest_static.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p, C.c_float,
                                       C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.pakr_batch_create.argtypes = [C.POINTER(ProblemDesc), C.POINTER(BatchQuery), C.c_int32, C.POINTER(C.c_void_p)]
+    L.pakr_batch_destroy.argtypes = [C.c_void_p]
+    L.pakr_batch_destroy.restype = None
+    L.pakr_batch_plan.argtypes = [C.c_void_p, C.c_double, C.c_int64, C.c_uint64, C.c_uint32, C.POINTER(BatchResult)]
+    L.pakr_batch_path.argtypes = [C.c_void_p, C.c_int32, _PF, _PF, _PI32, C.c_int32]
+    L.pakr_batch_autotune.argtypes = [C.c_void_p, C.c_int64, C.c_uint64, C.POINTER(BatchTuning)]
+    L.pakr_batch_set_tuning.argtypes = [C.c_void_p, C.POINTER(BatchTuning)]
     for name in EXPORTED:
         fn = getattr(L, name)
-        if fn.restype is C.c_int or name in ("pakr_workspace_size",):
+        if name not in ("pakr_destroy", "pakr_batch_destroy", "pakr_last_error", "pakr_version"):
             fn.restype = C.c_int
     _lib = L
     return L
@@ -148,6 +177,31 @@ def _pf(a):
     return a.ctypes.data_as(_PF)
 
 
+def problem_desc(spec, arr):
+    """A ProblemDesc for a problem dict; arr() turns a host array into a kept-alive pointer."""
+    desc = ProblemDesc()
+    desc.dynamics = spec["dyn"]
+    desc.x_lo, desc.x_hi = arr(spec["x_lo"]), arr(spec["x_hi"])
+    desc.u_lo, desc.u_hi = arr(spec["u_lo"]), arr(spec["u_hi"])
+    desc.dt = spec["dt"]
+    desc.steps_min, desc.steps_max = spec["s_min"], spec["s_max"]
+    boxes = np.asarray(spec["boxes"]).reshape(-1)
+    spheres = np.asarray(spec["spheres"]).reshape(-1)
+    desc.n_boxes = int(np.asarray(spec["boxes"]).shape[0])
+    desc.boxes = arr(boxes) if boxes.size else None
+    desc.n_spheres = int(np.asarray(spec["spheres"]).shape[0])
+    desc.spheres = arr(spheres) if spheres.size else None
+    desc.goal_radius = spec["goal_r"]
+    desc.cost = spec.get("cost", COST_PATH_LENGTH)
+    desc.heuristic = spec.get("heuristic", H_POSITION)
+    desc.heuristic_speed = spec.get("h_speed", 0.0)
+    desc.nn_weights = arr(spec["nn_w"]) if spec.get("nn_w") is not None else None
+    desc.model_params = arr(spec["model"]) if spec["dyn"] == QUAD12 else None
+    desc.n_parents, desc.branching = spec["K"], spec["k"]
+    desc.tree_cap = spec["cap"]
+    return desc
+
+
 class Planner:
     """One planning problem on one GPU (a pakr_planner handle).
 
@@ -172,24 +226,7 @@ class Planner:
             keep.append(a)
             return _pf(a)
 
-        desc = ProblemDesc()
-        desc.dynamics = spec["dyn"]
-        desc.x_lo, desc.x_hi = arr(spec["x_lo"]), arr(spec["x_hi"])
-        desc.u_lo, desc.u_hi = arr(spec["u_lo"]), arr(spec["u_hi"])
-        desc.dt = spec["dt"]
-        desc.steps_min, desc.steps_max = spec["s_min"], spec["s_max"]
-        boxes = np.asarray(spec["boxes"]).reshape(-1)
-        spheres = np.asarray(spec["spheres"]).reshape(-1)
-        desc.n_boxes = int(np.asarray(spec["boxes"]).shape[0])
-        desc.boxes = arr(boxes) if boxes.size else None
-        desc.n_spheres = int(np.asarray(spec["spheres"]).shape[0])
-        desc.spheres = arr(spheres) if spheres.size else None
-        desc.goal_radius = spec["goal_r"]
-        desc.cost = spec.get("cost", COST_PATH_LENGTH)
-        desc.heuristic = spec.get("heuristic", H_POSITION)
-        desc.heuristic_speed = spec.get("h_speed", 0.0)
-        desc.nn_weights = arr(spec["nn_w"]) if spec.get("nn_w") is not None else None
-        desc.model_params = arr(spec["model"]) if spec["dyn"] == QUAD12 else None
+        desc = problem_desc(spec, arr)
         desc.n_parents, desc.branching = self.K, self.k
         desc.tree_cap = self.cap
         desc.device = device
@@ -333,3 +370,81 @@ class Planner:
         _check(lib().pakr_philox4x32_10(self.h, ctr.ctypes.data_as(P32), k.ctypes.data_as(P32),
                                         out.ctypes.data_as(P32), ctr.shape[0]), "pakr_philox4x32_10")
         return out
+
+
+class BatchPlanner:
+    """Many independent planning queries advanced by one persistent launch
+    (pakr_batch_*).  ``base`` is a problem dict (its obstacles and cap are not
+    used); each query is a dict with x_init, x_goal, boxes, spheres and cap."""
+
+    def __init__(self, base, queries, device=0, stream=None, path_cap=1024):
+        import torch
+
+        self.d, self.m = base["d"], base["m"]
+        self.nq = len(queries)
+        self._keep = []
+        keep = self._keep
+
+        def arr(v):
+            a = _f32(v).reshape(-1)
+            keep.append(a)
+            return _pf(a)
+
+        desc = problem_desc(base, arr)
+        desc.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        desc.cuda_stream = C.c_void_p(stream.cuda_stream)
+        desc.path_cap = path_cap
+        self.path_cap = path_cap
+        qs = (BatchQuery * self.nq)()
+        for i, q in enumerate(queries):
+            qs[i].x_init, qs[i].x_goal = arr(q["x_init"]), arr(q["x_goal"])
+            b = np.asarray(q["boxes"])
+            sp = np.asarray(q.get("spheres", np.zeros((0, base["pdim"] + 1))))
+            qs[i].n_boxes = int(b.shape[0])
+            qs[i].boxes = arr(b) if b.size else None
+            qs[i].n_spheres = int(sp.shape[0])
+            qs[i].spheres = arr(sp) if sp.size else None
+            qs[i].tree_cap = int(q["cap"])
+        self._qs = qs
+        h = C.c_void_p()
+        _check(lib().pakr_batch_create(C.byref(desc), qs, self.nq, C.byref(h)), "pakr_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().pakr_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def plan(self, budget_s=1.0, max_iterations=0, seed=0, stop_at_first=False):
+        res = (BatchResult * self.nq)()
+        flags = PLAN_STOP_AT_FIRST if stop_at_first else 0
+        _check(lib().pakr_batch_plan(self.h, float(budget_s), int(max_iterations), int(seed), flags, res),
+               "pakr_batch_plan")
+        return [{f: getattr(r, f) for f, _ in BatchResult._fields_ if f != "reserved"} for r in res]
+
+    def path(self, q, max_edges=None):
+        max_edges = self.path_cap if max_edges is None else max_edges
+        states = np.zeros((max_edges + 1, self.d), np.float32)
+        controls = np.zeros((max(max_edges, 1), self.m), np.float32)
+        steps = np.zeros(max(max_edges, 1), np.int32)
+        _check(lib().pakr_batch_path(self.h, int(q), _pf(states), _pf(controls), steps.ctypes.data_as(_PI32),
+                                     max_edges), "pakr_batch_path")
+        return states, controls, steps
+
+    def autotune(self, iterations=3, seed=0):
+        t = BatchTuning()
+        _check(lib().pakr_batch_autotune(self.h, int(iterations), int(seed), C.byref(t)), "pakr_batch_autotune")
+        return dict(block_threads=t.block_threads, nn_chunk=t.nn_chunk, n_tried=t.n_tried, best_ms=t.best_ms)
+
+    def set_tuning(self, block_threads, nn_chunk):
+        t = BatchTuning(block_threads, nn_chunk, 0, 0.0)
+        return _check(lib().pakr_batch_set_tuning(self.h, C.byref(t)), "pakr_batch_set_tuning")

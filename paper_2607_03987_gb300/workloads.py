@@ -150,3 +150,26 @@ def prefilled_tree(spec, n, seed, cost_hi=0.0):
     steps[0] = 0
     return dict(states=states, controls=controls, parents=parents, costs=costs, steps=steps, count=n,
                 iteration=0)
+
+
+def batch_queries(n_queries=256, env_seed=0, obs_range=(10, 200), cap_range=(64 * 1024, 1 << 20), min_sep=0.6):
+    """Independent 3D double-integrator queries: per query an obstacle count
+    uniform in obs_range, a tree cap uniform in cap_range (a multiple of
+    1024), and a random start / goal pair at rest, at least min_sep apart,
+    kept free of that query's boxes."""
+    rng = np.random.Generator(np.random.Philox(int(env_seed) + 7919))
+    base = problem("di3", env_seed=env_seed)
+    out = []
+    for _ in range(n_queries):
+        while True:
+            s = rng.uniform(0.08, 0.92, 3)
+            g = rng.uniform(0.08, 0.92, 3)
+            if np.linalg.norm(s - g) >= min_sep:
+                break
+        start = f32(np.concatenate([s, np.zeros(3)]))
+        goal = f32(np.concatenate([g, np.zeros(3)]))
+        n_obs = int(rng.integers(obs_range[0], obs_range[1] + 1))
+        boxes = _boxes(rng, n_obs, 3, 0.05, 0.2, [start, goal], base["goal_r"] + 0.02)
+        cap = int(rng.integers(cap_range[0] // 1024, cap_range[1] // 1024 + 1)) * 1024
+        out.append(dict(x_init=start, x_goal=goal, boxes=boxes, spheres=np.zeros((0, 4)), cap=cap))
+    return base, out
