@@ -113,6 +113,11 @@ class PlanOut(C.Structure):
     ]
 
 
+class TrajParams(C.Structure):
+    _fields_ = [("w_dur", C.c_double), ("w_u", C.c_double), ("w_obs", C.c_double), ("beta", C.c_double),
+                ("margin", C.c_double), ("w_goal", C.c_double), ("w_len", C.c_double), ("len_eps", C.c_double)]
+
+
 _lib = None
 
 
@@ -144,6 +149,11 @@ def lib():
         L.ora_extract_path.argtypes = [C.POINTER(Tree), C.c_int64, _PI64, C.c_int64]
         L.ora_extract_path.restype = C.c_int64
         L.ora_plan.argtypes = [C.POINTER(Problem), C.POINTER(Tree), _PD, C.c_uint64, C.POINTER(PlanOut)]
+        L.ora_traj_cost.argtypes = [C.POINTER(Problem), _PD, _PD, C.c_int, C.POINTER(TrajParams), _PD]
+        L.ora_traj_cost.restype = C.c_double
+        L.ora_traj_grad.argtypes = [C.POINTER(Problem), _PD, _PD, C.c_int, C.POINTER(TrajParams), _PD, _PD]
+        L.ora_traj_grad.restype = C.c_double
+        L.ora_dynamics_vjp.argtypes = [C.POINTER(Problem), _PD, _PD, _PD, _PD, _PD]
         L.ora_recheck_edge_dense.argtypes = [C.POINTER(Problem), _PD, _PD, C.c_int, C.c_int]
         L.ora_di_edge_hits_exact.argtypes = [C.POINTER(Problem), _PD, _PD, C.c_int]
         _lib = L
@@ -403,3 +413,35 @@ def recheck_edge_dense(prob, x0, u, S, sub=16):
 def di_edge_hits_exact(prob, x0, u, S):
     x0, u = _f64(x0), _f64(u)
     return bool(lib().ora_di_edge_hits_exact(prob.ref, _pd(x0), _pd(u), int(S)))
+
+
+TRAJ_DEFAULTS = dict(w_dur=1.0, w_u=0.1, w_obs=1.0, beta=50.0, margin=0.0, w_goal=1.0, w_len=0.0, len_eps=1e-3)
+
+
+def traj_params(**kw):
+    w = dict(TRAJ_DEFAULTS)
+    w.update(kw)
+    return TrajParams(**w)
+
+
+def dynamics_vjp(prob, x, u, a):
+    x, u, a = _f64(x), _f64(u), _f64(a)
+    gx, gu = np.zeros(prob.P.d), np.zeros(prob.P.m)
+    lib().ora_dynamics_vjp(prob.ref, _pd(x), _pd(u), _pd(a), _pd(gx), _pd(gu))
+    return gx, gu
+
+
+def traj_cost(prob, x0, U, w=None):
+    x0, U = _f64(x0), _f64(U)
+    w = traj_params() if w is None else w
+    xf = np.zeros(prob.P.d)
+    J = lib().ora_traj_cost(prob.ref, _pd(x0), _pd(U), U.shape[0], C.byref(w), _pd(xf))
+    return J, xf
+
+
+def traj_grad(prob, x0, U, w=None):
+    x0, U = _f64(x0), _f64(U)
+    w = traj_params() if w is None else w
+    dU, dx0 = np.zeros_like(U), np.zeros(prob.P.d)
+    J = lib().ora_traj_grad(prob.ref, _pd(x0), _pd(U), U.shape[0], C.byref(w), _pd(dU), _pd(dx0))
+    return J, dU, dx0

@@ -829,3 +829,346 @@ int ora_di_edge_hits_exact(const ora_problem *P, const double *x0, const double 
         return ora_recheck_edge_dense(P, x0, u, S, 64);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Smooth trajectory cost and its discrete adjoint (reverse mode through each  */
+/* RK4 step).  Test infrastructure for the refinement kernels.                 */
+/* ------------------------------------------------------------------------- */
+
+/* a^T (df/dx), a^T (df/du) of the dynamics at (x, u). */
+void ora_dynamics_vjp(const ora_problem *P, const double *x, const double *u, const double *a, double *gx,
+                      double *gu)
+{
+    int d = P->d, m = P->m;
+    for (int i = 0; i < d; ++i)
+        gx[i] = 0.0;
+    for (int j = 0; j < m; ++j)
+        gu[j] = 0.0;
+    switch (P->dyn) {
+    case ORA_DI2:
+    case ORA_DI3: {
+        /* p' = v, v' = u */
+        int pd = P->pdim;
+        for (int i = 0; i < pd; ++i) {
+            gx[pd + i] += a[i];
+            gu[i] += a[pd + i];
+        }
+        break;
+    }
+    case ORA_QUAD12: {
+        double mass = P->model[0], Ixx = P->model[1], Iyy = P->model[2], Izz = P->model[3], g = P->model[4];
+        double phi = x[3], th = x[4], psi = x[5];
+        double cf = cos(phi), sf = sin(phi), ct = cos(th), st = sin(th), cp = cos(psi), sp = sin(psi);
+        double tt = st / ct;
+        double v[3] = {x[6], x[7], x[8]}, w[3] = {x[9], x[10], x[11]};
+        const double *ap = a, *ae = a + 3, *av = a + 6, *aw = a + 9;
+        double R[3][3] = {{cp * ct, cp * st * sf - sp * cf, cp * st * cf + sp * sf},
+                          {sp * ct, sp * st * sf + cp * cf, sp * st * cf - cp * sf},
+                          {-st, ct * sf, ct * cf}};
+        double dRf[3][3] = {{0, cp * st * cf + sp * sf, -cp * st * sf + sp * cf},
+                            {0, sp * st * cf - cp * sf, -sp * st * sf - cp * cf},
+                            {0, ct * cf, -ct * sf}};
+        double dRt[3][3] = {{-cp * st, cp * ct * sf, cp * ct * cf},
+                            {-sp * st, sp * ct * sf, sp * ct * cf},
+                            {-ct, -st * sf, -st * cf}};
+        double dRp[3][3] = {{-sp * ct, -sp * st * sf - cp * cf, -sp * st * cf + cp * sf},
+                            {cp * ct, cp * st * sf - sp * cf, cp * st * cf + sp * sf},
+                            {0, 0, 0}};
+        /* p' = R v */
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                gx[6 + c] += R[r][c] * ap[r];
+                gx[3] += ap[r] * dRf[r][c] * v[c];
+                gx[4] += ap[r] * dRt[r][c] * v[c];
+                gx[5] += ap[r] * dRp[r][c] * v[c];
+            }
+        /* eta' = W omega */
+        double W[3][3] = {{1, sf * tt, cf * tt}, {0, cf, -sf}, {0, sf / ct, cf / ct}};
+        double dWf[3][3] = {{0, cf * tt, -sf * tt}, {0, -sf, -cf}, {0, cf / ct, -sf / ct}};
+        double c2 = ct * ct;
+        double dWt[3][3] = {{0, sf / c2, cf / c2}, {0, 0, 0}, {0, sf * st / c2, cf * st / c2}};
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                gx[9 + c] += W[r][c] * ae[r];
+                gx[3] += ae[r] * dWf[r][c] * w[c];
+                gx[4] += ae[r] * dWt[r][c] * w[c];
+            }
+        /* v' = v x w - g (third row of R) + T/m e3 */
+        /* a . (v x w) = v . (w x a) = w . (a x v) */
+        gx[6] += w[1] * av[2] - w[2] * av[1];
+        gx[7] += w[2] * av[0] - w[0] * av[2];
+        gx[8] += w[0] * av[1] - w[1] * av[0];
+        gx[9] += av[1] * v[2] - av[2] * v[1];
+        gx[10] += av[2] * v[0] - av[0] * v[2];
+        gx[11] += av[0] * v[1] - av[1] * v[0];
+        for (int c = 0; c < 3; ++c) {
+            gx[3] += -g * av[c] * dRf[2][c];
+            gx[4] += -g * av[c] * dRt[2][c];
+        }
+        gu[0] += av[2] / mass;
+        /* w' = I^-1 (tau - w x I w) */
+        double p_ = w[0], q_ = w[1], r_ = w[2];
+        gu[1] += aw[0] / Ixx;
+        gu[2] += aw[1] / Iyy;
+        gu[3] += aw[2] / Izz;
+        gx[9] += -(Ixx - Izz) * r_ * aw[1] / Iyy - (Iyy - Ixx) * q_ * aw[2] / Izz;
+        gx[10] += -(Izz - Iyy) * r_ * aw[0] / Ixx - (Iyy - Ixx) * p_ * aw[2] / Izz;
+        gx[11] += -(Izz - Iyy) * q_ * aw[0] / Ixx - (Ixx - Izz) * p_ * aw[1] / Iyy;
+        break;
+    }
+    case ORA_DUBINS3D: {
+        double yaw = x[3], pitch = x[4], vv = x[5];
+        double cy = cos(yaw), sy = sin(yaw), cpi = cos(pitch), spi = sin(pitch);
+        gx[3] += a[0] * (-vv * cpi * sy) + a[1] * (vv * cpi * cy);
+        gx[4] += a[0] * (-vv * spi * cy) + a[1] * (-vv * spi * sy) + a[2] * (vv * cpi);
+        gx[5] += a[0] * cpi * cy + a[1] * cpi * sy + a[2] * spi;
+        gu[0] += a[3];
+        gu[1] += a[4];
+        gu[2] += a[5];
+        break;
+    }
+    case ORA_UNICYCLE1: {
+        double c = cos(x[2]), sn = sin(x[2]);
+        gx[2] += a[0] * (-u[0] * sn) + a[1] * (u[0] * c);
+        gu[0] += a[0] * c + a[1] * sn;
+        gu[1] += a[2];
+        break;
+    }
+    case ORA_UNICYCLE2: {
+        double c = cos(x[2]), sn = sin(x[2]);
+        gx[2] += a[0] * (-x[3] * sn) + a[1] * (x[3] * c);
+        gx[3] += a[0] * c + a[1] * sn;
+        gx[4] += a[2];
+        gu[0] += a[3];
+        gu[1] += a[4];
+        break;
+    }
+    default:
+        break;
+    }
+}
+
+/* Smallest signed distance from p to the obstacles (boxes: exact box SDF;
+ * spheres: |p - c| - r) summed over every obstacle is not what the penalty
+ * needs; this returns the SDF of one obstacle given by index, see below. */
+static double box_sdf(int pd, const double *lo, const double *hi, const double *p, double *grad)
+{
+    double q[3], out2 = 0.0, qmax = -INFINITY;
+    int amax = 0;
+    for (int a = 0; a < pd; ++a) {
+        double ql = lo[a] - p[a], qh = p[a] - hi[a];
+        q[a] = ql > qh ? ql : qh;
+        if (q[a] > 0)
+            out2 += q[a] * q[a];
+        if (q[a] > qmax) {
+            qmax = q[a];
+            amax = a;
+        }
+    }
+    for (int a = 0; a < pd; ++a)
+        grad[a] = 0.0;
+    if (out2 > 0) {
+        double o = sqrt(out2);
+        for (int a = 0; a < pd; ++a) {
+            if (q[a] > 0) {
+                double sgn = (lo[a] - p[a] > p[a] - hi[a]) ? -1.0 : 1.0;
+                grad[a] = sgn * q[a] / o;
+            }
+        }
+        return o;
+    }
+    grad[amax] = (lo[amax] - p[amax] > p[amax] - hi[amax]) ? -1.0 : 1.0;
+    return qmax;
+}
+
+static double softplus_b(double z, double beta)
+{
+    double bz = beta * z;
+    return (bz > 0 ? bz : 0.0) / beta + log1p(exp(-fabs(bz))) / beta;
+}
+
+static double sigmoid(double z)
+{
+    return z >= 0 ? 1.0 / (1.0 + exp(-z)) : exp(z) / (1.0 + exp(z));
+}
+
+/* Penalty sum_obstacles softplus_beta(margin - sdf(p)) and its gradient in p. */
+static double obstacle_penalty(const ora_problem *P, const ora_traj_params *w, const double *p, double *grad)
+{
+    int pd = P->pdim;
+    double total = 0.0, g[3];
+    for (int a = 0; a < pd; ++a)
+        grad[a] = 0.0;
+    for (int b = 0; b < P->n_boxes; ++b) {
+        const double *lo = P->boxes + (size_t)b * 2 * pd, *hi = lo + pd;
+        double sdf = box_sdf(pd, lo, hi, p, g);
+        double z = w->margin - sdf;
+        total += softplus_b(z, w->beta);
+        double s = sigmoid(w->beta * z);
+        for (int a = 0; a < pd; ++a)
+            grad[a] += -s * g[a];
+    }
+    for (int sidx = 0; sidx < P->n_spheres; ++sidx) {
+        const double *c = P->spheres + (size_t)sidx * (pd + 1);
+        double dd = 0.0;
+        for (int a = 0; a < pd; ++a)
+            dd += (p[a] - c[a]) * (p[a] - c[a]);
+        double dist = sqrt(dd);
+        double z = w->margin - (dist - c[pd]);
+        total += softplus_b(z, w->beta);
+        double s = sigmoid(w->beta * z);
+        for (int a = 0; a < pd; ++a)
+            grad[a] += dist > 0 ? -s * (p[a] - c[a]) / dist : 0.0;
+    }
+    return total;
+}
+
+double ora_obstacle_sdf(const ora_problem *P, const double *p, double *grad)
+{
+    /* signed distance to the nearest obstacle (diagnostic) */
+    int pd = P->pdim;
+    double best = INFINITY, g[3];
+    for (int b = 0; b < P->n_boxes; ++b) {
+        const double *lo = P->boxes + (size_t)b * 2 * pd, *hi = lo + pd;
+        double sdf = box_sdf(pd, lo, hi, p, g);
+        if (sdf < best) {
+            best = sdf;
+            for (int a = 0; a < pd; ++a)
+                grad[a] = g[a];
+        }
+    }
+    return best;
+}
+
+double ora_traj_cost(const ora_problem *P, const double *x0, const double *U, int N, const ora_traj_params *w,
+                     double *x_final)
+{
+    int d = P->d, m = P->m, pd = P->pdim;
+    double x[ORA_MAX_D], xn[ORA_MAX_D], g[3];
+    memcpy(x, x0, sizeof(double) * (size_t)d);
+    double J = w->w_dur * N * P->dt;
+    for (int n = 0; n < N; ++n) {
+        const double *u = U + (size_t)n * m;
+        for (int j = 0; j < m; ++j)
+            J += w->w_u * u[j] * u[j] * P->dt;
+        ora_rk4_step(P, x, u, P->dt, xn);
+        double dd = 0.0;
+        for (int a = 0; a < pd; ++a)
+            dd += (xn[a] - x[a]) * (xn[a] - x[a]);
+        J += w->w_len * sqrt(dd + w->len_eps * w->len_eps);
+        memcpy(x, xn, sizeof(double) * (size_t)d);
+        J += w->w_obs * obstacle_penalty(P, w, x, g) * P->dt;
+    }
+    double e2 = 0.0;
+    for (int a = 0; a < pd; ++a)
+        e2 += (x[a] - P->x_goal[a]) * (x[a] - P->x_goal[a]);
+    J += w->w_goal * e2;
+    if (x_final)
+        memcpy(x_final, x, sizeof(double) * (size_t)d);
+    return J;
+}
+
+/* Reverse mode: store every state, then pull the adjoint back through each
+ * RK4 step's four stages.  Returns the cost; fills dJ/dU and dJ/dx0. */
+double ora_traj_grad(const ora_problem *P, const double *x0, const double *U, int N, const ora_traj_params *w,
+                     double *dU, double *dx0)
+{
+    int d = P->d, m = P->m, pd = P->pdim;
+    double h = P->dt;
+    double *X = (double *)malloc(sizeof(double) * (size_t)(N + 1) * d);
+    memcpy(X, x0, sizeof(double) * (size_t)d);
+    for (int n = 0; n < N; ++n)
+        ora_rk4_step(P, X + (size_t)n * d, U + (size_t)n * m, h, X + (size_t)(n + 1) * d);
+    double J = ora_traj_cost(P, x0, U, N, w, NULL);
+    double lam[ORA_MAX_D], g3[3];
+    /* adjoint of the final state: goal error + obstacle penalty at x_N */
+    for (int i = 0; i < d; ++i)
+        lam[i] = 0.0;
+    const double *xN = X + (size_t)N * d;
+    for (int a = 0; a < pd; ++a)
+        lam[a] += 2.0 * w->w_goal * (xN[a] - P->x_goal[a]);
+    obstacle_penalty(P, w, xN, g3);
+    for (int a = 0; a < pd; ++a)
+        lam[a] += w->w_obs * g3[a] * h;
+    for (int n = N - 1; n >= 0; --n) {
+        const double *xs = X + (size_t)n * d, *xe = X + (size_t)(n + 1) * d;
+        const double *u = U + (size_t)n * m;
+        /* path-length segment n -> n+1 */
+        double dd = 0.0;
+        for (int a = 0; a < pd; ++a)
+            dd += (xe[a] - xs[a]) * (xe[a] - xs[a]);
+        double L = sqrt(dd + w->len_eps * w->len_eps);
+        for (int a = 0; a < pd; ++a)
+            lam[a] += w->w_len * (xe[a] - xs[a]) / L;
+        /* stages of the forward step */
+        double k1[ORA_MAX_D], k2[ORA_MAX_D], k3[ORA_MAX_D], y2[ORA_MAX_D], y3[ORA_MAX_D], y4[ORA_MAX_D];
+        ora_dynamics(P, xs, u, k1);
+        for (int i = 0; i < d; ++i)
+            y2[i] = xs[i] + 0.5 * h * k1[i];
+        ora_dynamics(P, y2, u, k2);
+        for (int i = 0; i < d; ++i)
+            y3[i] = xs[i] + 0.5 * h * k2[i];
+        ora_dynamics(P, y3, u, k3);
+        for (int i = 0; i < d; ++i)
+            y4[i] = xs[i] + h * k3[i];
+        /* x' = x + h/6 (k1 + 2k2 + 2k3 + k4) */
+        double a1[ORA_MAX_D], a2[ORA_MAX_D], a3[ORA_MAX_D], a4[ORA_MAX_D], gx[ORA_MAX_D], gu[ORA_MAX_M];
+        double xb[ORA_MAX_D], ub[ORA_MAX_M];
+        for (int i = 0; i < d; ++i) {
+            xb[i] = lam[i];
+            a1[i] = h / 6.0 * lam[i];
+            a2[i] = h / 3.0 * lam[i];
+            a3[i] = h / 3.0 * lam[i];
+            a4[i] = h / 6.0 * lam[i];
+        }
+        for (int j = 0; j < m; ++j)
+            ub[j] = 2.0 * w->w_u * u[j] * h;
+        /* k4 = f(y4), y4 = x + h k3 */
+        ora_dynamics_vjp(P, y4, u, a4, gx, gu);
+        for (int i = 0; i < d; ++i) {
+            xb[i] += gx[i];
+            a3[i] += h * gx[i];
+        }
+        for (int j = 0; j < m; ++j)
+            ub[j] += gu[j];
+        /* k3 = f(y3), y3 = x + h/2 k2 */
+        ora_dynamics_vjp(P, y3, u, a3, gx, gu);
+        for (int i = 0; i < d; ++i) {
+            xb[i] += gx[i];
+            a2[i] += 0.5 * h * gx[i];
+        }
+        for (int j = 0; j < m; ++j)
+            ub[j] += gu[j];
+        /* k2 = f(y2), y2 = x + h/2 k1 */
+        ora_dynamics_vjp(P, y2, u, a2, gx, gu);
+        for (int i = 0; i < d; ++i) {
+            xb[i] += gx[i];
+            a1[i] += 0.5 * h * gx[i];
+        }
+        for (int j = 0; j < m; ++j)
+            ub[j] += gu[j];
+        /* k1 = f(x) */
+        ora_dynamics_vjp(P, xs, u, a1, gx, gu);
+        for (int i = 0; i < d; ++i)
+            xb[i] += gx[i];
+        for (int j = 0; j < m; ++j)
+            ub[j] += gu[j];
+        for (int j = 0; j < m; ++j)
+            dU[(size_t)n * m + j] = ub[j];
+        /* adjoint of x_n: the step's pull-back, the other end of the segment,
+         * and the obstacle penalty at x_n (states 1..N carry it) */
+        for (int i = 0; i < d; ++i)
+            lam[i] = xb[i];
+        for (int a = 0; a < pd; ++a)
+            lam[a] -= w->w_len * (xe[a] - xs[a]) / L;
+        if (n >= 1) {
+            obstacle_penalty(P, w, xs, g3);
+            for (int a = 0; a < pd; ++a)
+                lam[a] += w->w_obs * g3[a] * h;
+        }
+    }
+    if (dx0)
+        memcpy(dx0, lam, sizeof(double) * (size_t)d);
+    free(X);
+    return J;
+}

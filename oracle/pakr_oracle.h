@@ -150,6 +150,23 @@ typedef struct {
 } ora_plan_out;
 int ora_plan(const ora_problem *P, ora_tree *T, const double *x_init, uint64_t seed, ora_plan_out *o);
 
+/* --- smooth trajectory cost and its reverse-mode gradient (adjoint RK4) ---
+ * Trajectory: x_{n+1} = RK4(x_n, u_n, dt), n = 0..N-1, controls row-major
+ * U[n*m + j].  Cost
+ *   J = w_dur N dt + w_u sum_n |u_n|^2 dt + w_obs sum_{n=1..N} sum_obstacles softplus_beta(margin - sdf(p_n)) dt
+ *       + w_goal |p_N - p_goal|^2 + w_len sum_n sqrt(|p_{n+1} - p_n|^2 + eps^2),
+ * softplus_beta(z) = log(1 + exp(beta z)) / beta.  Not part of the paper. */
+typedef struct {
+    double w_dur, w_u, w_obs, beta, margin, w_goal, w_len, len_eps;
+} ora_traj_params;
+double ora_traj_cost(const ora_problem *P, const double *x0, const double *U, int N, const ora_traj_params *w,
+                     double *x_final);
+double ora_traj_grad(const ora_problem *P, const double *x0, const double *U, int N, const ora_traj_params *w,
+                     double *dU, double *dx0);
+void ora_dynamics_vjp(const ora_problem *P, const double *x, const double *u, const double *a, double *gx,
+                      double *gu);
+double ora_obstacle_sdf(const ora_problem *P, const double *p, double *grad);
+
 /* --- validation-only dense re-checks --- */
 int ora_recheck_edge_dense(const ora_problem *P, const double *x0, const double *u, int S, int sub);
 int ora_di_edge_hits_exact(const ora_problem *P, const double *x0, const double *u, int S);
