@@ -342,6 +342,52 @@ pakr_status pakr_batch_autotune(pakr_batch *batch, int64_t iterations, uint64_t 
 /* Set the launch shape directly (for example, a cached autotuner result). */
 pakr_status pakr_batch_set_tuning(pakr_batch *batch, const pakr_batch_tuning *tuning);
 
+/* ---------------------------------------------------------------------------
+ * Smooth trajectory cost and its gradient (adjoint RK4), for refining AO-x
+ * solutions by gradient descent.  The paper has no counterpart: it is a
+ * refinement step around Algorithm 1, not part of it.
+ *
+ * A trajectory t starts at x0[t*d..] and applies control
+ * controls[(t*n_steps + n)*m + j] during RK4 step n (n = 0..n_steps-1) of the
+ * planner's dt.  Cost
+ *   J = w_duration n_steps dt + w_control sum_n |u_n|^2 dt
+ *     + w_obstacle sum_{n=1..N} sum_obstacles softplus_beta(margin - sdf(p_n)) dt
+ *     + w_goal |p_N - p_goal|^2 + w_length sum_n sqrt(|p_{n+1} - p_n|^2 + length_eps^2)
+ * with softplus_beta(z) = log(1 + exp(beta z)) / beta, the exact box signed
+ * distance and |p - c| - r for spheres, over the planner's obstacles.  The
+ * duration term is constant in the controls (the step count is fixed).
+ * All arrays are device memory; x_goal is host memory (d floats).  The calls
+ * enqueue on the planner's stream.
+ * ------------------------------------------------------------------------- */
+typedef struct pakr_traj_params {
+    float w_duration, w_control, w_obstacle, beta, margin, w_goal, w_length, length_eps;
+} pakr_traj_params;
+
+/* cost[t] (and x_final[t*d..] if not NULL) for n_traj trajectories. */
+pakr_status pakr_traj_cost(pakr_planner *planner, const float *x0, const float *controls, int32_t n_traj,
+                           int32_t n_steps, const float *x_goal, const pakr_traj_params *params, float *cost,
+                           float *x_final);
+
+/* controls_grad = cost_grad[t] * dJ_t/dU (cost_grad NULL = 1) and, if not
+ * NULL, x0_grad = cost_grad[t] * dJ_t/dx0, by a forward sweep that keeps the
+ * state every 16 steps in checkpoints (pakr_traj_checkpoint_floats floats,
+ * caller-owned device scratch) and a backward sweep that recomputes each
+ * 16-step segment and pulls the adjoint back through every RK4 stage. */
+pakr_status pakr_traj_grad(pakr_planner *planner, const float *x0, const float *controls, int32_t n_traj,
+                           int32_t n_steps, const float *x_goal, const pakr_traj_params *params,
+                           const float *cost_grad, float *controls_grad, float *x0_grad, float *checkpoints);
+
+/* Size in floats of the checkpoint scratch pakr_traj_grad needs (-1 on a bad argument). */
+int64_t pakr_traj_checkpoint_floats(const pakr_planner *planner, int32_t n_traj, int32_t n_steps);
+
+/* The planner's rules on control sequences: valid[t] = 1 if every state after
+ * a step lies in the state box and no obstacle; in_goal[t] = 1 if the final
+ * position lies in the goal ball; path_length[t] = sum of |p_{n+1} - p_n|.
+ * in_goal, path_length and x_final may be NULL. */
+pakr_status pakr_traj_check(pakr_planner *planner, const float *x0, const float *controls, int32_t n_traj,
+                            int32_t n_steps, const float *x_goal, int32_t *valid, int32_t *in_goal,
+                            float *path_length, float *x_final);
+
 /* Cost-pruned nearest neighbour that allocates no device memory.
  *
  * The paper has no counterpart of this call: it exists for callers that

@@ -399,6 +399,10 @@ pakr_status pakr::fill_problem(const pakr_problem_desc *desc, DevProblem *P, int
     return PAKR_OK;
 }
 
+const DevProblem *pakr::planner_problem(const pakr_planner *p) { return &p->P; }
+cudaStream_t pakr::planner_stream(const pakr_planner *p) { return p->stream; }
+int pakr::planner_device(const pakr_planner *p) { return p->device; }
+
 extern "C" {
 
 const char *pakr_version(void) { return "pakr-gb300 0.1 (sm_103a)"; }

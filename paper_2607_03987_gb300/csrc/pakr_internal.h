@@ -142,6 +142,11 @@ cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_
 // Sets the calling thread's pakr_last_error() message (pakr_api.cu).
 void record_error(const char *msg);
 
+// Planner internals for the other translation units (pakr_api.cu).
+const DevProblem *planner_problem(const pakr_planner *p);
+cudaStream_t planner_stream(const pakr_planner *p);
+int planner_device(const pakr_planner *p);
+
 // Validates the problem part of a description (not obstacles or tree size)
 // and fills the kernel constants (pakr_api.cu).
 pakr_status fill_problem(const pakr_problem_desc *desc, DevProblem *P, int *d, int *m, int *pdim);

@@ -78,6 +78,11 @@ class Path(C.Structure):
     ]
 
 
+class TrajParams(C.Structure):
+    _fields_ = [(n, C.c_float) for n in ("w_duration", "w_control", "w_obstacle", "beta", "margin", "w_goal",
+                                         "w_length", "length_eps")]
+
+
 class BatchQuery(C.Structure):
     _fields_ = [
         ("x_init", _PF), ("x_goal", _PF), ("n_boxes", C.c_int32), ("boxes", _PF),
@@ -103,7 +108,7 @@ EXPORTED = [
     "pakr_expand", "pakr_plan", "pakr_tree_export", "pakr_tree_import", "pakr_tree_truncate", "pakr_debug_last_expand",
     "pakr_set_profiling", "pakr_kernel_times", "pakr_philox4x32_10", "pakr_nearest_static", "pakr_version",
     "pakr_batch_create", "pakr_batch_destroy", "pakr_batch_plan", "pakr_batch_path", "pakr_batch_autotune",
-    "pakr_batch_set_tuning",
+    "pakr_batch_set_tuning", "pakr_traj_cost", "pakr_traj_grad", "pakr_traj_checkpoint_floats", "pakr_traj_check",
 ]
 
 _lib = None
@@ -148,10 +153,17 @@ def lib():
     L.pakr_batch_path.argtypes = [C.c_void_p, C.c_int32, _PF, _PF, _PI32, C.c_int32]
     L.pakr_batch_autotune.argtypes = [C.c_void_p, C.c_int64, C.c_uint64, C.POINTER(BatchTuning)]
     L.pakr_batch_set_tuning.argtypes = [C.c_void_p, C.POINTER(BatchTuning)]
+    _vp = C.c_void_p
+    L.pakr_traj_cost.argtypes = [_vp, _vp, _vp, C.c_int32, C.c_int32, _PF, C.POINTER(TrajParams), _vp, _vp]
+    L.pakr_traj_grad.argtypes = [_vp, _vp, _vp, C.c_int32, C.c_int32, _PF, C.POINTER(TrajParams), _vp, _vp, _vp,
+                                 _vp]
+    L.pakr_traj_checkpoint_floats.argtypes = [_vp, C.c_int32, C.c_int32]
+    L.pakr_traj_check.argtypes = [_vp, _vp, _vp, C.c_int32, C.c_int32, _PF, _vp, _vp, _vp, _vp]
     for name in EXPORTED:
         fn = getattr(L, name)
         if name not in ("pakr_destroy", "pakr_batch_destroy", "pakr_last_error", "pakr_version"):
             fn.restype = C.c_int
+    L.pakr_traj_checkpoint_floats.restype = C.c_int64
     _lib = L
     return L
 
