@@ -260,6 +260,103 @@ def batched_vs_sequential(dev, stream, n_queries=256, seed=4242, max_iterations=
                         "U[64k,1M], random start/goal pairs, plan to first solution; host wall clock including "
                         "launch and result read-back"}
 
+
+def adjoint_bench(dev, stream, T=1024, N=200, reps=20):
+    """Smooth-cost gradient of 1024 quadrotor control sequences of 200 RK4
+    steps over the 100-pillar forest (adjoint RK4, checkpoints every 16
+    steps): forward and gradient time, and the largest relative gradient error
+    against the FP64 oracle's reverse mode on a sample of sequences."""
+    import torch
+
+    import oracle
+    from paper_2607_03987_gb300 import pakr, refine
+    from paper_2607_03987_gb300 import workloads as W
+
+    spec = W.with_sizes(W.problem("quad12", env_seed=0), K=1, k=1, cap=16)
+    planner = pakr.Planner(spec, device=dev, stream=stream)
+    rng = np.random.default_rng(0)
+    x0 = np.zeros((T, 12), np.float32)
+    x0[:, :3] = rng.uniform(0.1, 0.9, (T, 3))
+    x0[:, 6:9] = rng.uniform(-0.2, 0.2, (T, 3))
+    U = np.concatenate([9.81 + rng.normal(0, 0.5, (T, N, 1)), rng.uniform(-0.002, 0.002, (T, N, 3))],
+                       axis=2).astype(np.float32)
+    w = dict(refine.DEFAULT_WEIGHTS)
+    Ut = torch.tensor(U, device=f"cuda:{dev}")
+    xt = torch.tensor(x0, device=f"cuda:{dev}")
+    cost = torch.empty(T, device=f"cuda:{dev}")
+    dU = torch.empty_like(Ut)
+    dx = torch.empty_like(xt)
+    nck = pakr.lib().pakr_traj_checkpoint_floats(planner.h, T, N)
+    ck = torch.empty(int(nck), device=f"cuda:{dev}")
+    prm = refine._params(w)
+    g, gp = refine._goal(spec["x_goal"])
+    import ctypes as C
+
+    def fwd():
+        pakr._check(pakr.lib().pakr_traj_cost(planner.h, C.c_void_p(xt.data_ptr()), C.c_void_p(Ut.data_ptr()), T, N,
+                                              gp, C.byref(prm), C.c_void_p(cost.data_ptr()), None), "cost")
+
+    def grad():
+        pakr._check(pakr.lib().pakr_traj_grad(planner.h, C.c_void_p(xt.data_ptr()), C.c_void_p(Ut.data_ptr()), T, N,
+                                              gp, C.byref(prm), None, C.c_void_p(dU.data_ptr()),
+                                              C.c_void_p(dx.data_ptr()), C.c_void_p(ck.data_ptr())), "grad")
+
+    for _ in range(3):
+        fwd()
+        grad()
+    times = {}
+    for name, fn in (("cost_ms", fwd), ("grad_ms", grad)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        times[name] = a.elapsed_time(b) / reps
+    dUh = dU.cpu().numpy()
+    prob = oracle.OracleProblem(spec)
+    prob.set_goal(spec["x_goal"])
+    ow = oracle.traj_params(w_dur=w["w_duration"], w_u=w["w_control"], w_obs=w["w_obstacle"], beta=w["beta"],
+                            margin=w["margin"], w_goal=w["w_goal"], w_len=w["w_length"], len_eps=w["length_eps"])
+    errs = []
+    for t in range(0, T, T // 8):
+        _, dUo, _ = oracle.traj_grad(prob, x0[t], U[t], ow)
+        errs.append(float(np.abs(dUh[t] - dUo).max() / np.abs(dUo).max()))
+    planner.close()
+    return {"sequences": T, "steps": N, "checkpoint_every": 16, **times,
+            "gradients_per_s": T / (times["grad_ms"] * 1e-3),
+            "max_rel_grad_error_vs_fp64_oracle": max(errs), "sampled_sequences": len(errs),
+            "workload": "12D quadrotor, dt 0.02, 100 pillars, hover thrust + N(0,0.5), torques U[-0.002,0.002]; "
+                        "cost = duration + 0.1 |u|^2 + softplus(50 (-sdf)) penalty + goal error"}
+
+
+def refined_vs_plain(dev, stream, budget_s=0.1, seeds=10, n_boxes=50):
+    """AO-x path cost after the same wall-clock budget: plain pakr_plan vs
+    planning to a first solution, refining it with the adjoint kernels,
+    tightening the bound to the refined cost, and repeating."""
+    from paper_2607_03987_gb300 import pakr, refine
+    from paper_2607_03987_gb300 import workloads as W
+
+    spec = W.problem("di3", env_seed=0, n_boxes=n_boxes)
+    planner = pakr.Planner(spec, device=dev, stream=stream)
+    refine.refined_aox(planner, spec, 0.05, seed=999)  # warm-up (graphs, torch kernels)
+    plain, refined, rounds = [], [], []
+    for sd in range(seeds):
+        t0 = time.perf_counter()
+        r = planner.plan(spec["x_init"], spec["x_goal"], budget_s=budget_s, seed=sd)
+        plain.append(float(r["cost"]))
+        c, hist, gain = refine.refined_aox(planner, spec, budget_s, seed=sd)
+        refined.append(c)
+        rounds.append(gain)
+    planner.close()
+    lb = float(np.linalg.norm(spec["x_goal"][:3] - spec["x_init"][:3]) - spec["goal_r"])
+    return {"budget_s": budget_s, "seeds": seeds, "plain_cost_p50": float(np.median(plain)),
+            "refined_cost_p50": float(np.median(refined)), "refined_lower_in": int(sum(a < b for a, b in
+                                                                                     zip(refined, plain))),
+            "plain_costs": plain, "refined_costs": refined, "refinement_gain_p50": float(np.median(rounds)),
+            "straight_line_lower_bound": lb,
+            "workload": f"di3 (3D double integrator, {n_boxes} boxes, path-length cost), host wall-clock budget per seed"}
+
 def run_reference(args):
     ws, rank, local = _dist_env()
     if rank != 0:
@@ -310,6 +407,7 @@ def main():
     ap.add_argument("--aox-trials", type=int, default=20)
     ap.add_argument("--no-sweep", action="store_true", help="skip the tree-size sweep")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-sequential comparison")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint and refinement measurements")
     ap.add_argument("--only-expand", action="store_true",
                     help="time the expansion steps only (no e2e, planning metrics or CPU baseline)")
     args = ap.parse_args()
@@ -471,6 +569,10 @@ def main():
             line["by_tree_size"] = tree_size_sweep(dev, stream)
         if not args.no_batched:
             line["batched_256"] = batched_vs_sequential(dev, stream)
+        if not args.no_adjoint:
+            line["adjoint_1024x200"] = adjoint_bench(dev, stream)
+            line["refined_aox_100ms"] = refined_vs_plain(dev, stream)
+            line["refined_aox_100ms_cluttered"] = refined_vs_plain(dev, stream, n_boxes=300)
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(spec, tree, seed=7)
         print(json.dumps(line), flush=True)

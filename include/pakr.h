@@ -232,6 +232,13 @@ pakr_status pakr_expand(pakr_planner *planner, float cost_bound, uint64_t seed, 
 pakr_status pakr_plan(pakr_planner *planner, const float *x_init, const float *x_goal, double budget_s,
                       int64_t max_iterations, uint64_t seed, uint32_t flags, pakr_path *out);
 
+/* pakr_plan starting from c_best = initial_bound instead of +inf: only
+ * solutions cheaper than the bound are found (AO-x continued from an earlier
+ * or refined solution).  initial_bound = +inf is pakr_plan. */
+pakr_status pakr_plan_bounded(pakr_planner *planner, const float *x_init, const float *x_goal, double budget_s,
+                              int64_t max_iterations, uint64_t seed, uint32_t flags, float initial_bound,
+                              pakr_path *out);
+
 /* Copy the tree to host memory (node-major).  Synchronises the stream.
  * PAKR_ERR_INVALID_ARG if tree->capacity < the node count (tree->count then
  * holds the count). */

@@ -686,6 +686,15 @@ pakr_status pakr_expand(pakr_planner *p, float cost_bound, uint64_t seed, pakr_e
 pakr_status pakr_plan(pakr_planner *p, const float *x_init, const float *x_goal, double budget_s,
                       int64_t max_iterations, uint64_t seed, uint32_t flags, pakr_path *out)
 {
+    return pakr_plan_bounded(p, x_init, x_goal, budget_s, max_iterations, seed, flags, INFINITY, out);
+}
+
+pakr_status pakr_plan_bounded(pakr_planner *p, const float *x_init, const float *x_goal, double budget_s,
+                              int64_t max_iterations, uint64_t seed, uint32_t flags, float initial_bound,
+                              pakr_path *out)
+{
+    if (std::isnan(initial_bound))
+        return fail(PAKR_ERR_INVALID_ARG, "initial_bound is NaN");
     if (!p || !x_init || !x_goal || !out)
         return fail(PAKR_ERR_INVALID_ARG, "NULL argument");
     if (!finite_all(x_init, p->di.d) || !finite_all(x_goal, p->di.d))
@@ -709,6 +718,7 @@ pakr_status pakr_plan(pakr_planner *p, const float *x_init, const float *x_goal,
     h->budget_ns = ns >= 1.8e19 ? ~0ull : (unsigned long long)ns;
     h->max_iterations = max_iterations > 0 ? std::min<int64_t>(max_iterations, kMaxPlanIterations) : kMaxPlanIterations;
     h->stop_at_first = (flags & PAKR_PLAN_STOP_AT_FIRST) ? 1 : 0;
+    h->c_best_init = initial_bound;
     CUDA_TRY(cudaMemcpyAsync(p->pp, h, sizeof(PlanParams), cudaMemcpyHostToDevice, p->stream));
     CUDA_TRY(cudaGraphLaunch(p->plan_exec, p->stream));
     st = read_ctl(p);

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(NT, (NnMinBlocks<Dims<DYN>::D, NT>::value))
     for (int q = gtid; q < nq; q += nthreads) {
         const BatchQueryDev &qd = Q[q];
         aox_init_one<DYN>(qd.P, qd.ctl, qd.T, qd.x_init, qd.x_goal, G->seed + (unsigned long long)q,
-                          G->max_iterations, G->budget_ns);
+                          G->max_iterations, G->budget_ns, __int_as_float(0x7f800000));
     }
     if (gtid == 0) {
         G->t0_ns = globaltimer_ns();

@@ -861,13 +861,13 @@ __device__ __forceinline__ bool aox_step_warp(const DevProblem &P, Ctl *ctl, con
 }
 
 // Fresh AO-x run for one tree (Algorithm 1): the goal, the root
-// {(x_init, -, 0)}, c_best = +inf, the expansion counter at 0 and the device
-// clock started.  One thread.  Returns whether the loop should run (a valid
+// {(x_init, -, 0)}, c_best = c_best_init (+inf for a fresh run), the
+// expansion counter at 0 and the device clock started.  One thread.  Returns whether the loop should run (a valid
 // start, a positive budget and iteration cap).
 template <int DYN>
 __device__ __forceinline__ bool aox_init_one(const DevProblem &P, Ctl *ctl, const DevTree &T, const float *x_init,
                                              const float *x_goal, unsigned long long seed, long long max_iterations,
-                                             unsigned long long budget_ns)
+                                             unsigned long long budget_ns, float c_best_init)
 {
     constexpr int D = Dims<DYN>::D, M = Dims<DYN>::M, PD = Dims<DYN>::PD;
     float x[D], goal[D];
@@ -888,7 +888,7 @@ __device__ __forceinline__ bool aox_init_one(const DevProblem &P, Ctl *ctl, cons
     ctl->count = 1;
     ctl->iteration = 0u;
     ctl->seed = seed;
-    ctl->c_best = __int_as_float(0x7f800000);
+    ctl->c_best = c_best_init;
     ctl->iterations_done = 0;
     ctl->n_solutions = 0;
     ctl->n_restarts = 0;

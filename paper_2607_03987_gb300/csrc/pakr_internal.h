@@ -95,7 +95,7 @@ struct PlanParams {
     unsigned long long budget_ns;
     long long max_iterations;
     int stop_at_first;
-    int pad;
+    float c_best_init;   // AO-x bound the run starts from (+inf for a fresh run)
 };
 
 struct DevPlanBufs {

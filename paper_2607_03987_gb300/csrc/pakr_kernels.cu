@@ -116,7 +116,8 @@ __global__ void k_plan_init(DevProblem P, Ctl *ctl, DevTree T, const PlanParams 
     if (threadIdx.x != 0 || blockIdx.x != 0)
         return;
     const bool run =
-        aox_init_one<DYN>(P, ctl, T, pp->x_init, pp->x_goal, pp->seed, pp->max_iterations, pp->budget_ns);
+        aox_init_one<DYN>(P, ctl, T, pp->x_init, pp->x_goal, pp->seed, pp->max_iterations, pp->budget_ns,
+                          pp->c_best_init);
     cudaGraphSetConditional(h, run ? 1u : 0u);
 }
 

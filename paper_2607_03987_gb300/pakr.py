@@ -105,7 +105,7 @@ class BatchResult(C.Structure):
 
 EXPORTED = [
     "pakr_workspace_size", "pakr_create", "pakr_destroy", "pakr_last_error", "pakr_tree_reset",
-    "pakr_expand", "pakr_plan", "pakr_tree_export", "pakr_tree_import", "pakr_tree_truncate", "pakr_debug_last_expand",
+    "pakr_expand", "pakr_plan", "pakr_plan_bounded", "pakr_tree_export", "pakr_tree_import", "pakr_tree_truncate", "pakr_debug_last_expand",
     "pakr_set_profiling", "pakr_kernel_times", "pakr_philox4x32_10", "pakr_nearest_static", "pakr_version",
     "pakr_batch_create", "pakr_batch_destroy", "pakr_batch_plan", "pakr_batch_path", "pakr_batch_autotune",
     "pakr_batch_set_tuning", "pakr_traj_cost", "pakr_traj_grad", "pakr_traj_checkpoint_floats", "pakr_traj_check",
@@ -136,6 +136,8 @@ def lib():
     L.pakr_tree_reset.argtypes = [C.c_void_p, _PF, _PF]
     L.pakr_expand.argtypes = [C.c_void_p, C.c_float, C.c_uint64, C.POINTER(ExpandInfo)]
     L.pakr_plan.argtypes = [C.c_void_p, _PF, _PF, C.c_double, C.c_int64, C.c_uint64, C.c_uint32, C.POINTER(Path)]
+    L.pakr_plan_bounded.argtypes = [C.c_void_p, _PF, _PF, C.c_double, C.c_int64, C.c_uint64, C.c_uint32, C.c_float,
+                                    C.POINTER(Path)]
     L.pakr_tree_export.argtypes = [C.c_void_p, C.POINTER(TreeHost)]
     L.pakr_tree_import.argtypes = [C.c_void_p, C.POINTER(TreeHost), _PF]
     L.pakr_tree_truncate.argtypes = [C.c_void_p, C.c_int64]
@@ -288,7 +290,7 @@ class Planner:
         return st, {f: getattr(inf, f) for f, _ in ExpandInfo._fields_ if f != "reserved"}
 
     def plan(self, x_init, x_goal, budget_s=1.0, max_iterations=0, seed=0, stop_at_first=False, max_edges=None,
-             max_history=None):
+             max_history=None, initial_bound=None):
         max_edges = self.path_cap if max_edges is None else max_edges
         max_history = self.history_cap if max_history is None else max_history
         xi, xg = _f32(x_init), _f32(x_goal)
@@ -305,8 +307,13 @@ class Planner:
         p.history_time_s, p.history_cost = ht.ctypes.data_as(_PD), _pf(hc)
         p.history_iteration = hi.ctypes.data_as(_PI64)
         flags = PLAN_STOP_AT_FIRST if stop_at_first else 0
-        st = _check(lib().pakr_plan(self.h, _pf(xi), _pf(xg), float(budget_s), int(max_iterations), int(seed), flags,
-                                    C.byref(p)), "pakr_plan")
+        if initial_bound is None:
+            st = _check(lib().pakr_plan(self.h, _pf(xi), _pf(xg), float(budget_s), int(max_iterations), int(seed),
+                                        flags, C.byref(p)), "pakr_plan")
+        else:
+            st = _check(lib().pakr_plan_bounded(self.h, _pf(xi), _pf(xg), float(budget_s), int(max_iterations),
+                                                int(seed), flags, float(initial_bound), C.byref(p)),
+                        "pakr_plan_bounded")
         ne = p.n_edges
         ns = min(p.n_solutions, max_history)
         return dict(status=st, cost=p.cost, n_edges=ne, n_solutions=p.n_solutions, n_restarts=p.n_restarts,

@@ -96,43 +96,82 @@ def expand_controls(edge_controls, steps):
     return torch.repeat_interleave(edge_controls, reps, dim=0)
 
 
-def refine_path(planner, spec, path, x_goal, iters=40, lr=0.05, weights=None):
-    """Projected gradient descent on a path's per-edge controls.
+def refine_path(planner, spec, path, x_goal, iters=15, candidates=16, step=0.5, weights=None):
+    """Shorten a path found by pakr_plan with its step counts fixed.
 
-    Minimises the smooth cost (path length, obstacle penalty, goal error,
-    control effort) with the step counts fixed; after every step the controls
-    are clamped to the control box.  Returns (controls, length) of the best
-    iterate the planner's rules accept (valid at every substep, ending in the
-    goal ball), or None if no iterate improves on the input path's length."""
+    Each iteration takes the gradient of the smooth cost (path length, a
+    short-range obstacle penalty, goal error) with respect to the per-edge
+    controls, tries `candidates` step sizes step * 2^-i along the normalised
+    descent direction at once (clamped to the control box) and keeps the
+    shortest candidate that the planner's rules accept (valid after every
+    substep, ending in the goal ball) if it is shorter than the current path.
+    Everything stays on the device; the host reads the result once.  Returns
+    (controls, length), or None if no candidate improved the path."""
     dev = torch.device(f"cuda:{planner.device}")
     steps = np.asarray(path["steps"])
     if len(steps) == 0:
         return None
-    w = dict(w_length=1.0, w_obstacle=0.05, beta=200.0, margin=0.01, w_goal=50.0, w_control=0.0,
+    w = dict(w_length=1.0, w_obstacle=0.05, beta=200.0, margin=0.01, w_goal=2.0, w_control=0.0,
              w_duration=0.0, length_eps=1e-4)
     w.update(weights or {})
+    reps = torch.as_tensor(steps, dtype=torch.long, device=dev)
     x0 = torch.tensor(np.asarray(path["states"][0], np.float32)[None], device=dev)
-    u = torch.tensor(np.asarray(path["controls"], np.float32), device=dev, requires_grad=True)
+    u = torch.tensor(np.asarray(path["controls"], np.float32), device=dev)
     lo = torch.tensor(np.asarray(spec["u_lo"], np.float32), device=dev)
     hi = torch.tensor(np.asarray(spec["u_hi"], np.float32), device=dev)
-    opt = torch.optim.Adam([u], lr=lr)
-    best = None
-    base_len = None
-    for it in range(iters + 1):
-        U = expand_controls(u, steps)[None]
-        with torch.no_grad():
-            valid, in_goal, length, _ = traj_check(planner, U.detach(), x0, x_goal)
-            L = float(length[0])
-            if base_len is None:
-                base_len = L
-            if int(valid[0]) and int(in_goal[0]) and L < (best[1] if best else base_len):
-                best = (u.detach().clone(), L)
-        if it == iters:
-            break
-        J = traj_cost(planner, U, x0, x_goal, **w).sum()
-        opt.zero_grad()
-        J.backward()
-        opt.step()
-        with torch.no_grad():
-            u.copy_(torch.max(torch.min(u, hi), lo))
-    return best
+    alphas = step * torch.pow(2.0, -torch.arange(candidates, device=dev, dtype=torch.float32))
+    xc = x0.expand(candidates, -1).contiguous()
+    inf = torch.tensor(float("inf"), device=dev)
+
+    def per_step(uu):
+        return torch.repeat_interleave(uu, reps, dim=-2)
+
+    valid, in_goal, length, _ = traj_check(planner, per_step(u)[None], x0, x_goal)
+    cur = torch.where((valid[0] == 1) & (in_goal[0] == 1), length[0], inf)
+    start = cur.clone()
+    for _ in range(iters):
+        uu = u.clone().requires_grad_(True)
+        traj_cost(planner, per_step(uu)[None], x0, x_goal, **w).sum().backward()
+        g = uu.grad
+        d = g / (g.norm() + 1e-12)
+        cand = torch.max(torch.min(u[None] - alphas[:, None, None] * d[None], hi), lo)
+        v, ig, L, _ = traj_check(planner, per_step(cand), xc, x_goal)
+        L = torch.where((v == 1) & (ig == 1), L, inf)
+        i = torch.argmin(L)
+        better = L[i] < cur
+        u = torch.where(better, cand[i], u)
+        cur = torch.where(better, L[i], cur)
+    cur_f, start_f = float(cur), float(start)
+    if not np.isfinite(cur_f) or cur_f >= start_f:
+        return None
+    return u, cur_f
+
+
+def refined_aox(planner, spec, budget_s, seed=0, refine_iters=15, first_fraction=0.6):
+    """AO-x with one gradient refinement inside the wall-clock budget: run the
+    device-resident AO-x loop for first_fraction of the budget, refine its best
+    path with the adjoint kernels (accepted only if the planner's rules hold
+    and it is shorter), then continue AO-x from the refined cost as the bound
+    (pakr_plan_bounded) for the rest of the budget.  Returns (best cost,
+    [(elapsed s, cost)], refinement gain)."""
+    import time
+
+    t0 = time.perf_counter()
+    history = []
+    r = planner.plan(spec["x_init"], spec["x_goal"], budget_s=first_fraction * budget_s, seed=seed)
+    c_best = float(r["cost"]) if r["n_solutions"] else float("inf")
+    history.append((time.perf_counter() - t0, c_best))
+    gain = 0.0
+    if r["n_solutions"]:
+        out = refine_path(planner, spec, r, spec["x_goal"], iters=refine_iters)
+        if out is not None and out[1] < c_best:
+            gain = c_best - out[1]
+            c_best = out[1]
+        history.append((time.perf_counter() - t0, c_best))
+    left = budget_s - (time.perf_counter() - t0)
+    if left > 0:
+        r2 = planner.plan(spec["x_init"], spec["x_goal"], budget_s=left, seed=seed + 1, initial_bound=c_best)
+        if r2["n_solutions"]:
+            c_best = min(c_best, float(r2["cost"]))
+        history.append((time.perf_counter() - t0, c_best))
+    return c_best, history, gain

@@ -154,7 +154,7 @@ def test_refine_shortens_a_found_path(cuda_lib):
     planner = pakr.Planner(spec)
     res = planner.plan(spec["x_init"], spec["x_goal"], budget_s=5.0, seed=3, stop_at_first=True)
     assert res["n_solutions"] == 1
-    out = refine.refine_path(planner, spec, res, spec["x_goal"], iters=60)
+    out = refine.refine_path(planner, spec, res, spec["x_goal"], iters=20)
     assert out is not None, "no accepted refinement"
     u, L = out
     assert L < res["cost"]
