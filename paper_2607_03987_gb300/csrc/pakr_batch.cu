@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(NT, (NnMinBlocks<Dims<DYN>::D, NT>::value))
             const int n = qd.ctl->n_start;
             const int start = chunk * nn_chunk;
             const int end = min(n, start + nn_chunk);
-            nn_scan<D, kBatchQP, NT, kBatchNnTile, kBatchNnGroup, true>(qd.P, qd.T, qd.W, qd.ctl->bound,
+            nn_scan<D, kBatchQP, NT, kBatchNnTile, kBatchNnGroup>(qd.P, qd.T, qd.W, qd.ctl->bound,
                                                                        qg * NT * 2 * kBatchQP, start, end, smem);
         }
         grid.sync();
@@ -600,7 +600,7 @@ pakr_status pakr_batch_create(const pakr_problem_desc *base, const pakr_batch_qu
     if (e != cudaSuccess)
         return cleanup(bfail(PAKR_ERR_CUDA, "batch upload failed: %s", cudaGetErrorString(e)));
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
-    const size_t nn_tile = (size_t)kBatchNnTile * ((2 * d + 3) / 4 * 4) * sizeof(float);
+    const size_t nn_tile = (size_t)kBatchNnTile * ((2 * d + 2 + 3) / 4 * 4) * sizeof(float);
     const size_t obs_bytes = (size_t)max_obs * sizeof(float4) + kMaxD * sizeof(float);
     b->smem = std::max(nn_tile, obs_bytes);
     *out = b;

@@ -302,27 +302,32 @@ __device__ __forceinline__ void begin_batch(Ctl *ctl, float bound)
 // ---------------------------------------------------------------------------
 // k_nn: cost-pruned brute-force nearest neighbour.
 //
-// Block (chunk c, query group g): 2*QP queries per thread in registers,
-// nodes [c*per, (c+1)*per) streamed in TILE-node tiles through shared memory.
-// A tile row holds the node's negated coordinates (scaled by the square roots
-// of the NN weights), so q - x is one FADD.  PACKED keeps the queries as QP
-// float2 pairs and duplicates each coordinate in the row, (-x0,-x0,-x1,...),
-// so one FADD2 / FFMA2 serves two queries; the scalar form keeps 2*QP queries
-// and single coordinates.  Packed and scalar IEEE operations round alike, so
-// both give the same distance bits.
+// Result: for each query the eligible node (f-cost below the bound) with the
+// smallest exact FP32 squared distance  e = sum_a fl(q_a - x_a)^2  (FADD then
+// FMA per coordinate, in coordinate order), the lowest index on a tie.
 //
-// Ineligible nodes (f-cost not below the bound) and padding get +inf in
-// coordinate 0: their squared distance is +inf and never wins.  The argmin is
-// lazy: each group of G consecutive nodes yields a running minimum per query
-// (one FMNMX per pair); a strictly smaller group minimum replaces the best
-// distance and records that group.  After the chunk, each query recomputes
-// the distances of its best group from global memory with the same
-// operations and keeps the first node that reaches the best: nodes are
-// visited in ascending order and only a strictly smaller group minimum
-// replaces the best, so a tie resolves to the lowest index.  Across threads
-// and chunks the packed key (distance bits << 32 | index) is merged with
-// atomicMin, ordering by distance and then by index (non-negative floats
-// order like their IEEE bits).
+// Scan: block (chunk c, query group g) holds 2*QP queries per thread as QP
+// float2 pairs and streams its node range in TILE-node tiles through shared
+// memory.  The scan ranks nodes by the expanded form
+//     a = (|q|^2 + |x|^2) + sum_a q_a (-2 x_a),
+// one packed FFMA2 per coordinate for two queries (a tile row holds
+// (|x|^2, |x|^2, -2x_0, -2x_0, ...)), about half the FP32 work of the exact
+// form.  For every group of G consecutive nodes it keeps a running minimum
+// (one FMNMX per pair) and per query the two smallest group minima m1 <= m2
+// with their groups.  Ineligible nodes and padding carry |x|^2 = +inf.
+//
+// Exactness: rounding error analysis bounds |a - e| <= B = 2 gamma_{3D+3}
+// (|q| + X)^2 with gamma_k = k u / (1 - k u), u = 2^-24, X the largest node
+// norm of the chunk.  After the scan each query recomputes the exact form on
+// its best group (first node of the group minimum on a tie).  Every node of
+// another group has e >= m2 - B, so if m2 - B exceeds that exact minimum the
+// exact argmin of the chunk lies in the best group; otherwise the second group
+// is recomputed too, and if m2 - B still does not exceed the best exact value
+// the whole block rescans the chunk exactly for that query (nodes spread over
+// the threads, a warp minimum of the packed keys).  The answer is therefore
+// the exact argmin, bit for bit.  Across threads and chunks the key
+// (distance bits << 32 | index) is merged with atomicMin, ordering by
+// distance and then by index (non-negative floats order like their bits).
 // ---------------------------------------------------------------------------
 // Resident blocks per SM the register budget is set for: about 80 registers
 // per thread for D <= 6, 128 for D = 12.
@@ -331,64 +336,91 @@ struct NnMinBlocks {
     static constexpr int value = 65536 / (NT * (D <= 6 ? 80 : 128));
 };
 
-// First node of the group [j0, j0 + G) whose squared distance to the query
-// equals best; eligibility and arithmetic exactly as the tile staging and the
-// scan loop apply them.
-template <int D, int G>
-__device__ __forceinline__ int resolve_group(const DevProblem &P, const DevTree &T, int j0, int end, float bound,
-                                             const float *qv, float best)
+// Exact FP32 squared distance of node j to query qv, or +inf if ineligible.
+template <int D>
+__device__ __forceinline__ float exact_dist2(const DevProblem &P, const DevTree &T, int j, float bound, const float *qv)
 {
-    for (int g = 0; g < G; ++g) {
-        const int j = j0 + g;
-        if (j >= end)
-            break;
-        if (!(T.fcost[j] < bound))
-            continue;
-        float acc = 0.f;
+    if (!(T.fcost[j] < bound))
+        return __int_as_float(0x7f800000);
+    float acc = 0.f;
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            const float nx = -(T.X[(size_t)a * P.cap + j] * P.sw[a]);
-            const float diff = __fadd_rn(qv[a], nx);
-            acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
-        }
-        if (acc == best)
-            return j;
+    for (int a = 0; a < D; ++a) {
+        const float nx = -(T.X[(size_t)a * P.cap + j] * P.sw[a]);
+        const float diff = __fadd_rn(qv[a], nx);
+        acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
     }
-    return j0;  // not reached: the group minimum came from one of its nodes
+    return acc;
 }
 
+// Exact minimum over the group [j0, j0 + G) (nodes below end): smallest
+// distance, lowest index on a tie; all loads issued before the comparisons.
+template <int D, int G>
+__device__ __forceinline__ void exact_min_group(const DevProblem &P, const DevTree &T, int j0, int end, float bound,
+                                                const float *qv, float &best, int &bidx)
+{
+    float e[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+        e[g] = (j0 + g < end) ? exact_dist2<D>(P, T, j0 + g, bound, qv) : __int_as_float(0x7f800000);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const int j = j0 + g;
+        if (e[g] < best || (e[g] == best && j < bidx)) {
+            best = e[g];
+            bidx = j;
+        }
+    }
+}
+
+// Queries per block whose chunk is rescanned cooperatively (more fall back to a per-thread scan).
+constexpr int kNnFlagCap = 64;
+
+// gamma_k of rounding error analysis for FP32 (u = 2^-24).
+__host__ __device__ constexpr float nn_gamma(int k) { return (k * 5.9604645e-8f) / (1.f - k * 5.9604645e-8f); }
+
 // One block's scan: 2*QP queries per thread starting at query qbase, nodes
-// [start, end) in tiles; merges each query's result into W.nn_key.
-template <int D, int QP, int NT, int TILE, int G, bool PACKED>
+// [start, end) in tiles; merges each query's result into W.nn_key.  All
+// threads of the block must call it (it synchronises the block).
+template <int D, int QP, int NT, int TILE, int G>
 __device__ __forceinline__ void nn_scan(const DevProblem &P, const DevTree &T, const DevWork &W, float bound,
                                         int qbase, int start, int end, float *s_node)
 {
-    constexpr int NQ = 2 * QP;                                       // queries per thread
-    constexpr int RW = PACKED ? (2 * D + 3) / 4 * 4 : (D + 3) / 4 * 4;  // floats per tile row
+    constexpr int NQ = 2 * QP;                     // queries per thread
+    constexpr int RW = (2 * D + 2 + 3) / 4 * 4;    // floats per tile row
     constexpr int RV = RW / 4;
     static_assert(TILE % G == 0, "tile must hold whole groups");
+    __shared__ float s_xmax[NT / 32];
+    __shared__ int s_nflag;
+    __shared__ int s_flag_qid[kNnFlagCap];
+    __shared__ float s_flag_q[kNnFlagCap][D];
     const int K = P.K;
     const int cap = P.cap;
     const int tid = threadIdx.x;
     const float inf = __int_as_float(0x7f800000);
 
     // query qi of this thread is qbase + qi * NT + tid; packed pair p holds queries 2p and 2p+1
-    float qs[NQ][D];
+    float qs[NQ][D], qn[NQ];
 #pragma unroll
     for (int qi = 0; qi < NQ; ++qi) {
         const int qid = qbase + qi * NT + tid;
+        float s = 0.f;
 #pragma unroll
-        for (int a = 0; a < D; ++a)
+        for (int a = 0; a < D; ++a) {
             qs[qi][a] = (qid < K) ? W.xr[(size_t)a * K + qid] * P.sw[a] : 0.f;
+            s = __fmaf_rn(qs[qi][a], qs[qi][a], s);
+        }
+        qn[qi] = s;
     }
-    float best[NQ];
-    int bgrp[NQ];
+    float m1[NQ], m2[NQ];
+    int g1[NQ], g2[NQ];
 #pragma unroll
     for (int qi = 0; qi < NQ; ++qi) {
-        best[qi] = inf;
-        bgrp[qi] = -1;
+        m1[qi] = inf;
+        m2[qi] = inf;
+        g1[qi] = -1;
+        g2[qi] = -1;
     }
-
+    float xmax2 = 0.f;  // largest eligible node norm this thread staged
     const float4 *s4 = reinterpret_cast<const float4 *>(s_node);
 
     for (int t0 = start; t0 < end; t0 += TILE) {
@@ -402,18 +434,20 @@ __device__ __forceinline__ void nn_scan(const DevProblem &P, const DevTree &T, c
 #pragma unroll
             for (int a = 0; a < RW; ++a)
                 row[a] = 0.f;
+            float xn = 0.f;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                float v = in ? T.X[(size_t)a * cap + j] * P.sw[a] : 0.f;
-                if (a == 0 && !ok)
-                    v = inf;
-                if (PACKED) {
-                    row[2 * a] = -v;
-                    row[2 * a + 1] = -v;
-                } else {
-                    row[a] = -v;
-                }
+                const float v = in ? T.X[(size_t)a * cap + j] * P.sw[a] : 0.f;
+                xn = __fmaf_rn(v, v, xn);
+                row[2 + 2 * a] = -2.f * v;
+                row[3 + 2 * a] = -2.f * v;
             }
+            if (ok)
+                xmax2 = fmaxf(xmax2, xn);
+            else
+                xn = inf;
+            row[0] = xn;
+            row[1] = xn;
             float4 *dst = reinterpret_cast<float4 *>(&s_node[e * RW]);
 #pragma unroll
             for (int c = 0; c < RV; ++c)
@@ -437,49 +471,112 @@ __device__ __forceinline__ void nn_scan(const DevProblem &P, const DevTree &T, c
                     nx[4 * c + 2] = t.z;
                     nx[4 * c + 3] = t.w;
                 }
-                if (PACKED) {
 #pragma unroll
-                    for (int p = 0; p < QP; ++p) {
-                        float2 acc;
+                for (int p = 0; p < QP; ++p) {
+                    float2 acc = __fadd2_rn(make_float2(qn[2 * p], qn[2 * p + 1]), make_float2(nx[0], nx[1]));
 #pragma unroll
-                        for (int a = 0; a < D; ++a) {
-                            const float2 diff = __fadd2_rn(make_float2(qs[2 * p][a], qs[2 * p + 1][a]),
-                                                           make_float2(nx[2 * a], nx[2 * a + 1]));
-                            acc = (a == 0) ? __fmul2_rn(diff, diff) : __ffma2_rn(diff, diff, acc);
-                        }
-                        m[2 * p] = fminf(m[2 * p], acc.x);
-                        m[2 * p + 1] = fminf(m[2 * p + 1], acc.y);
-                    }
-                } else {
-#pragma unroll
-                    for (int qi = 0; qi < NQ; ++qi) {
-                        float acc;
-#pragma unroll
-                        for (int a = 0; a < D; ++a) {
-                            const float diff = __fadd_rn(qs[qi][a], nx[a]);
-                            acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
-                        }
-                        m[qi] = fminf(m[qi], acc);
-                    }
+                    for (int a = 0; a < D; ++a)
+                        acc = __ffma2_rn(make_float2(qs[2 * p][a], qs[2 * p + 1][a]),
+                                         make_float2(nx[2 + 2 * a], nx[3 + 2 * a]), acc);
+                    m[2 * p] = fminf(m[2 * p], acc.x);
+                    m[2 * p + 1] = fminf(m[2 * p + 1], acc.y);
                 }
             }
+            const int grp = t0 + e0;
 #pragma unroll
             for (int qi = 0; qi < NQ; ++qi) {
-                const bool better = m[qi] < best[qi];
-                best[qi] = better ? m[qi] : best[qi];
-                bgrp[qi] = better ? t0 + e0 : bgrp[qi];
+                const bool c1 = m[qi] < m1[qi];
+                const bool c2 = m[qi] < m2[qi];
+                m2[qi] = c1 ? m1[qi] : (c2 ? m[qi] : m2[qi]);
+                g2[qi] = c1 ? g1[qi] : (c2 ? grp : g2[qi]);
+                m1[qi] = c1 ? m[qi] : m1[qi];
+                g1[qi] = c1 ? grp : g1[qi];
             }
         }
     }
+    // largest node norm of the chunk (a block-wide maximum)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        xmax2 = fmaxf(xmax2, __shfl_xor_sync(0xFFFFFFFFu, xmax2, o));
+    __syncthreads();
+    if ((tid & 31) == 0)
+        s_xmax[tid >> 5] = xmax2;
+    if (tid == 0)
+        s_nflag = 0;
+    __syncthreads();
+    float X2 = 0.f;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w)
+        X2 = fmaxf(X2, s_xmax[w]);
+    const float X = sqrtf(X2);
+    constexpr float kGamma = nn_gamma(3 * D + 3);
 #pragma unroll
     for (int qi = 0; qi < NQ; ++qi) {
         const int qid = qbase + qi * NT + tid;
-        if (qid < K && bgrp[qi] >= 0) {
-            const int j = resolve_group<D, G>(P, T, bgrp[qi], end, bound, qs[qi], best[qi]);
-            const unsigned long long key =
-                ((unsigned long long)__float_as_uint(best[qi]) << 32) | (unsigned long long)(uint32_t)j;
-            atomicMin(&W.nn_key[qid], key);
+        if (qid >= K || g1[qi] < 0 || !(m1[qi] < inf))
+            continue;
+        const float r = sqrtf(qn[qi]) + X;
+        const float B = 2.f * kGamma * r * r * 1.0001f;
+        float best = inf;
+        int bidx = 0x7FFFFFFF;
+        exact_min_group<D, G>(P, T, g1[qi], end, bound, qs[qi], best, bidx);
+        bool certain = m2[qi] - B > best;
+        if (!certain && g2[qi] >= 0) {
+            exact_min_group<D, G>(P, T, g2[qi], end, bound, qs[qi], best, bidx);
+            certain = m2[qi] - B > best;
         }
+        if (certain) {
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(best) << 32) | (unsigned long long)(uint32_t)bidx;
+            atomicMin(&W.nn_key[qid], key);
+        } else {
+            // a third group may be as close: the block rescans the chunk for this query below
+            const int slot = atomicAdd(&s_nflag, 1);
+            if (slot < kNnFlagCap) {
+                s_flag_qid[slot] = qid;
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+                    s_flag_q[slot][a] = qs[qi][a];
+            } else {
+                float b2 = inf;
+                int i2 = 0x7FFFFFFF;
+                for (int j = start; j < end; ++j) {
+                    const float e = exact_dist2<D>(P, T, j, bound, qs[qi]);
+                    if (e < b2) {
+                        b2 = e;
+                        i2 = j;
+                    }
+                }
+                if (b2 < inf)
+                    atomicMin(&W.nn_key[qid],
+                              ((unsigned long long)__float_as_uint(b2) << 32) | (unsigned long long)(uint32_t)i2);
+            }
+        }
+    }
+    __syncthreads();
+    // exact rescans of the flagged queries by the whole block (coalesced nodes, warp minimum)
+    const int nflag = min(s_nflag, kNnFlagCap);
+    for (int f = 0; f < nflag; ++f) {
+        float qv[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            qv[a] = s_flag_q[f][a];
+        unsigned long long key = kNoKey;
+        for (int j = start + tid; j < end; j += NT) {
+            const float e = exact_dist2<D>(P, T, j, bound, qv);
+            if (e < inf) {
+                const unsigned long long k =
+                    ((unsigned long long)__float_as_uint(e) << 32) | (unsigned long long)(uint32_t)j;
+                key = k < key ? k : key;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, key, o);
+            key = other < key ? other : key;
+        }
+        if ((tid & 31) == 0 && key != kNoKey)
+            atomicMin(&W.nn_key[s_flag_qid[f]], key);
     }
 }
 

@@ -35,17 +35,17 @@ __global__ void k_sample(DevProblem P, Ctl *ctl, DevWork W, float bound, unsigne
     }
 }
 
-template <int D, int QP, int NT, int TILE, int G, bool PACKED>
+template <int D, int QP, int NT, int TILE, int G>
 __global__ void __launch_bounds__(NT, (NnMinBlocks<D, NT>::value))
     k_nn(DevProblem P, const Ctl *__restrict__ ctl, DevTree T, DevWork W)
 {
-    constexpr int RW = PACKED ? (2 * D + 3) / 4 * 4 : (D + 3) / 4 * 4;
+    constexpr int RW = (2 * D + 2 + 3) / 4 * 4;
     __shared__ __align__(16) float s_node[TILE * RW];
     const int n = ctl->n_start;
     const int per = nn_chunk_nodes<G>(n, gridDim.x);
     const int start = blockIdx.x * per;
     const int end = min(n, start + per);
-    nn_scan<D, QP, NT, TILE, G, PACKED>(P, T, W, ctl->bound, blockIdx.y * NT * 2 * QP, start, end, s_node);
+    nn_scan<D, QP, NT, TILE, G>(P, T, W, ctl->bound, blockIdx.y * NT * 2 * QP, start, end, s_node);
 }
 
 template <int DYN, int LG>
@@ -169,7 +169,6 @@ __global__ void k_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t
 
 constexpr int kNnTile = 256;
 constexpr int kNnGroup = 8;
-constexpr bool kNnPacked = true;
 
 cudaError_t launch_sample(const DevProblem &P, Ctl *ctl, const DevWork &W, const LaunchCfg &L, float bound,
                           unsigned long long seed, int mode, cudaStream_t s)
@@ -185,9 +184,9 @@ static cudaError_t launch_nn_d(const DevProblem &P, const Ctl *ctl, const DevTre
 {
     const dim3 grid(L.nn_chunks, L.nn_qgroups);
     switch (L.nn_variant) {
-    case 0: k_nn<D, 1, 64, kNnTile, kNnGroup, kNnPacked><<<grid, 64, 0, s>>>(P, ctl, T, W); break;
-    case 1: k_nn<D, 1, 128, kNnTile, kNnGroup, kNnPacked><<<grid, 128, 0, s>>>(P, ctl, T, W); break;
-    default: k_nn<D, 2, 256, kNnTile, kNnGroup, kNnPacked><<<grid, 256, 0, s>>>(P, ctl, T, W); break;
+    case 0: k_nn<D, 1, 64, kNnTile, kNnGroup><<<grid, 64, 0, s>>>(P, ctl, T, W); break;
+    case 1: k_nn<D, 1, 128, kNnTile, kNnGroup><<<grid, 128, 0, s>>>(P, ctl, T, W); break;
+    default: k_nn<D, 2, 256, kNnTile, kNnGroup><<<grid, 256, 0, s>>>(P, ctl, T, W); break;
     }
     return cudaGetLastError();
 }
@@ -277,9 +276,9 @@ static int nn_occ(int variant)
 {
     int nb = 0;
     switch (variant) {
-    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nn<D, 1, 64, kNnTile, kNnGroup, kNnPacked>, 64, 0); break;
-    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nn<D, 1, 128, kNnTile, kNnGroup, kNnPacked>, 128, 0); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nn<D, 2, 256, kNnTile, kNnGroup, kNnPacked>, 256, 0); break;
+    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nn<D, 1, 64, kNnTile, kNnGroup>, 64, 0); break;
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nn<D, 1, 128, kNnTile, kNnGroup>, 128, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_nn<D, 2, 256, kNnTile, kNnGroup>, 256, 0); break;
     }
     return nb;
 }
