@@ -125,6 +125,11 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_nn launch on the bench workload
+# (n = 1,000,000 nodes, d = 6), from one ncu capture of the current kernel.
+NN_DRAM_BYTES_NCU = 28.10e6
+
+
 def nn_flops_per_launch(K, n, d):
     """Algorithmic FP32 work of one nearest-neighbour pass: a subtract, a
     multiply and an add per coordinate of every (query, node) pair."""
@@ -161,6 +166,43 @@ def cpu_baseline(spec, tree, seed, target_s=10.0):
             "sample": f"one expansion with {K1} of {spec['K']} parents x {spec['k']} controls on the same "
                       f"{N_PREFILL}-node tree ({rollouts} rollouts, {t1:.1f} s single-threaded FP64)"}
 
+
+
+def table4_sweep(dev, stream, trials=20, budget_s=1.0):
+    """Batch size and branching factor sensitivity on the 12D quadrotor
+    (Table 4): for batch B in {4k, 8k, 16k, 32k} rollouts and branching
+    factor A in {2, 16, 64, 128}, K = B / A parents per expansion.  Each
+    trial plans from a fresh tree to the first solution with the device AO-x
+    graph (budget_s per trial, seeds 0..trials-1); reported per cell: success
+    rate, median device time to the first solution, median expansions and
+    median tree size at that moment, and the median time per expansion
+    iteration (the rate the sweep compares across hardware)."""
+    from paper_2607_03987_gb300 import pakr
+    from paper_2607_03987_gb300 import workloads as W
+
+    out = []
+    for B in (4096, 8192, 16384, 32768):
+        for A in (2, 16, 64, 128):
+            spec = W.problem("quad12", env_seed=0, K=B // A, k=A)
+            planner = pakr.Planner(spec, device=dev, stream=stream)
+            planner.plan(spec["x_init"], spec["x_goal"], budget_s=0.2, seed=999, stop_at_first=True)
+            t_ms, iters, nodes, per_it, solved = [], [], [], [], 0
+            for sd in range(trials):
+                r = planner.plan(spec["x_init"], spec["x_goal"], budget_s=budget_s, seed=sd, stop_at_first=True)
+                if r["n_solutions"]:
+                    solved += 1
+                    t_ms.append(r["t_first_solution_s"] * 1e3)
+                    iters.append(r["iterations_first_solution"])
+                    nodes.append(r["nodes_first_solution"])
+                    per_it.append(r["t_first_solution_s"] * 1e3 / max(r["iterations_first_solution"], 1))
+            planner.close()
+            med = (lambda v: float(np.median(v)) if v else None)
+            out.append({"batch": B, "branching": A, "parents": B // A, "success": solved / trials,
+                        "time_ms_p50": med(t_ms), "iterations_p50": med(iters), "nodes_p50": med(nodes),
+                        "ms_per_iteration_p50": med(per_it)})
+    return {"workload": "12D quadrotor, 100-pillar forest, hover (0.1,0.1,0.5) -> goal ball (0.9,0.9,0.5) "
+                        "r=0.05, cap 4M, plan to the first solution", "trials": trials, "budget_s": budget_s,
+            "cells": out}
 
 
 def tree_size_sweep(dev, stream, steps=10, warmup=3):
@@ -408,6 +450,9 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the tree-size sweep")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-sequential comparison")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint and refinement measurements")
+    ap.add_argument("--table4", action="store_true",
+                    help="add the batch size x branching factor sweep on the 12D quadrotor (Table 4)")
+    ap.add_argument("--table4-trials", type=int, default=20)
     ap.add_argument("--only-expand", action="store_true",
                     help="time the expansion steps only (no e2e, planning metrics or CPU baseline)")
     args = ap.parse_args()
@@ -504,7 +549,8 @@ def main():
     fp32_peak_tflops = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = flops / (nn_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak_tflops, "traffic": None, "kernel": "k_nn",
+                "frac": achieved / fp32_peak_tflops, "traffic": NN_DRAM_BYTES_NCU, "kernel": "k_nn",
+                "traffic_unit": "DRAM bytes read + written per k_nn launch (ncu, this kernel and workload)",
                 "peak_source": f"FP32 FFMA: {props.multi_processor_count} SMs x 128 lanes x 2 flop x "
                                f"{sm_mhz:.0f} MHz ({peak_src} max SM clock)",
                 "nn_ms_per_launch": nn_ms,
@@ -573,6 +619,8 @@ def main():
             line["adjoint_1024x200"] = adjoint_bench(dev, stream)
             line["refined_aox_100ms"] = refined_vs_plain(dev, stream)
             line["refined_aox_100ms_cluttered"] = refined_vs_plain(dev, stream, n_boxes=300)
+        if args.table4:
+            line["table4_quad12"] = table4_sweep(dev, stream, trials=args.table4_trials)
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(spec, tree, seed=7)
         print(json.dumps(line), flush=True)

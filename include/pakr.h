@@ -169,6 +169,8 @@ typedef struct pakr_path {
     double t_first_solution_s;  /* device time to the first solution, < 0 if none */
     double t_total_s;           /* device time of the whole plan */
     int64_t iterations;         /* expansion iterations run */
+    int64_t nodes_first_solution;      /* tree size when the first solution was found, -1 if none */
+    int64_t iterations_first_solution; /* expansion iterations up to the first solution, -1 if none */
 } pakr_path;
 
 /* Plan flags. */
@@ -238,6 +240,11 @@ pakr_status pakr_plan(pakr_planner *planner, const float *x_init, const float *x
 pakr_status pakr_plan_bounded(pakr_planner *planner, const float *x_init, const float *x_goal, double budget_s,
                               int64_t max_iterations, uint64_t seed, uint32_t flags, float initial_bound,
                               pakr_path *out);
+
+/* Current node count of the tree (and the expansion counter, if iteration is
+ * not NULL).  Synchronises the stream; reads two words, not the tree.
+ * PAKR_ERR_INVALID_ARG if planner or count is NULL. */
+pakr_status pakr_tree_size(pakr_planner *planner, int64_t *count, uint32_t *iteration);
 
 /* Copy the tree to host memory (node-major).  Synchronises the stream.
  * PAKR_ERR_INVALID_ARG if tree->capacity < the node count (tree->count then
@@ -321,6 +328,8 @@ typedef struct pakr_batch_result {
     double t_first_solution_s;  /* device time to the first solution, < 0 if none */
     int32_t n_restarts;
     int32_t reserved;
+    int64_t nodes_first_solution;      /* tree size when the first solution was found, -1 if none */
+    int64_t iterations_first_solution; /* expansion iterations up to the first solution, -1 if none */
 } pakr_batch_result;
 
 /* base: the shared problem (its obstacles and tree_cap are ignored; path_cap

@@ -730,6 +730,8 @@ pakr_status pakr_plan_bounded(pakr_planner *p, const float *x_init, const float 
     out->n_restarts = c.n_restarts;
     out->iterations = c.iterations_done;
     out->t_first_solution_s = c.t_first_ns == ~0ull ? -1.0 : (double)c.t_first_ns * 1e-9;
+    out->nodes_first_solution = c.n_solutions > 0 ? c.nodes_first : -1;
+    out->iterations_first_solution = c.n_solutions > 0 ? c.iterations_first : -1;
     out->t_total_s = (double)(c.t_end_ns - c.t0_ns) * 1e-9;
     out->n_edges = 0;
     if (c.err)
@@ -775,6 +777,20 @@ pakr_status pakr_plan_bounded(pakr_planner *p, const float *x_init, const float 
     if (c.plan_status == 3)
         return PAKR_NO_ELIGIBLE;
     return PAKR_BUDGET_EXPIRED;
+}
+
+pakr_status pakr_tree_size(pakr_planner *p, int64_t *count, uint32_t *iteration)
+{
+    if (!p || !count)
+        return fail(PAKR_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard guard(p->device);
+    pakr_status st = read_ctl(p);
+    if (st != PAKR_OK)
+        return st;
+    *count = p->ctl_host->count;
+    if (iteration)
+        *iteration = p->ctl_host->iteration;
+    return PAKR_OK;
 }
 
 pakr_status pakr_tree_export(pakr_planner *p, pakr_tree_host *t)

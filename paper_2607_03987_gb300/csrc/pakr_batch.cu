@@ -659,6 +659,8 @@ pakr_status pakr_batch_plan(pakr_batch *b, double budget_s, int64_t max_iteratio
         r.n_edges = c.n_solutions > 0 ? (c.path_len > 0 ? c.path_len - 1 : -1) : 0;
         r.iterations = c.iterations_done;
         r.t_first_solution_s = c.t_first_ns == ~0ull ? -1.0 : (double)c.t_first_ns * 1e-9;
+        r.nodes_first_solution = c.n_solutions > 0 ? c.nodes_first : -1;
+        r.iterations_first_solution = c.n_solutions > 0 ? c.iterations_first : -1;
         r.n_restarts = c.n_restarts;
         if (c.plan_status == -1)
             r.status = PAKR_ERR_INVALID_ARG;

@@ -891,8 +891,11 @@ __device__ __forceinline__ bool aox_step_warp(const DevProblem &P, Ctl *ctl, con
                 B.hist_cost[ns] = c;
                 B.hist_iter[ns] = ctl->iterations_done - 1;
             }
-            if (ns == 0)
+            if (ns == 0) {
                 ctl->t_first_ns = now - ctl->t0_ns;
+                ctl->nodes_first = ctl->count;
+                ctl->iterations_first = ctl->iterations_done;
+            }
             ctl->n_solutions = ns + 1;
             // ExtractPath: length first, bounded by the node count.
             int len = 0;
@@ -992,6 +995,8 @@ __device__ __forceinline__ bool aox_init_one(const DevProblem &P, Ctl *ctl, cons
     ctl->path_len = 0;
     ctl->err = 0;
     ctl->t_first_ns = ~0ull;
+    ctl->nodes_first = -1;
+    ctl->iterations_first = -1;
     const bool valid = state_valid<D, PD>(x, P, P.boxes, P.n_boxes, P.spheres, P.n_spheres);
     ctl->plan_status = valid ? 0 : -1;
     const bool run = valid && max_iterations > 0 && budget_ns > 0;

@@ -81,6 +81,8 @@ struct Ctl {
     long long iterations_done;
     unsigned long long t0_ns;
     unsigned long long t_first_ns;
+    long long nodes_first;   // tree size when the first solution was recorded
+    long long iterations_first;
     unsigned long long t_end_ns;
     int n_solutions;
     int n_restarts;

@@ -75,6 +75,7 @@ class Path(C.Structure):
         ("history_iteration", _PI64),
         ("n_edges", C.c_int32), ("cost", C.c_float), ("n_solutions", C.c_int32), ("n_restarts", C.c_int32),
         ("t_first_solution_s", C.c_double), ("t_total_s", C.c_double), ("iterations", C.c_int64),
+        ("nodes_first_solution", C.c_int64), ("iterations_first_solution", C.c_int64),
     ]
 
 
@@ -99,13 +100,13 @@ class BatchResult(C.Structure):
     _fields_ = [
         ("status", C.c_int32), ("n_solutions", C.c_int32), ("cost", C.c_float), ("n_edges", C.c_int32),
         ("iterations", C.c_int64), ("t_first_solution_s", C.c_double), ("n_restarts", C.c_int32),
-        ("reserved", C.c_int32),
+        ("reserved", C.c_int32), ("nodes_first_solution", C.c_int64), ("iterations_first_solution", C.c_int64),
     ]
 
 
 EXPORTED = [
     "pakr_workspace_size", "pakr_create", "pakr_destroy", "pakr_last_error", "pakr_tree_reset",
-    "pakr_expand", "pakr_plan", "pakr_plan_bounded", "pakr_tree_export", "pakr_tree_import", "pakr_tree_truncate", "pakr_debug_last_expand",
+    "pakr_expand", "pakr_plan", "pakr_plan_bounded", "pakr_tree_export", "pakr_tree_size", "pakr_tree_import", "pakr_tree_truncate", "pakr_debug_last_expand",
     "pakr_set_profiling", "pakr_kernel_times", "pakr_philox4x32_10", "pakr_nearest_static", "pakr_version",
     "pakr_batch_create", "pakr_batch_destroy", "pakr_batch_plan", "pakr_batch_path", "pakr_batch_autotune",
     "pakr_batch_set_tuning", "pakr_traj_cost", "pakr_traj_grad", "pakr_traj_checkpoint_floats", "pakr_traj_check",
@@ -141,6 +142,7 @@ def lib():
     L.pakr_tree_export.argtypes = [C.c_void_p, C.POINTER(TreeHost)]
     L.pakr_tree_import.argtypes = [C.c_void_p, C.POINTER(TreeHost), _PF]
     L.pakr_tree_truncate.argtypes = [C.c_void_p, C.c_int64]
+    L.pakr_tree_size.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_uint32)]
     L.pakr_debug_last_expand.argtypes = [C.c_void_p, _PF, _PI32, C.POINTER(C.c_int8), _PF, _PI32]
     L.pakr_set_profiling.argtypes = [C.c_void_p, C.c_int32]
     L.pakr_kernel_times.argtypes = [C.c_void_p, _PD, _PI64, C.POINTER(C.c_char_p), C.c_int32]
@@ -318,6 +320,8 @@ class Planner:
         ns = min(p.n_solutions, max_history)
         return dict(status=st, cost=p.cost, n_edges=ne, n_solutions=p.n_solutions, n_restarts=p.n_restarts,
                     t_first_solution_s=p.t_first_solution_s, t_total_s=p.t_total_s, iterations=p.iterations,
+                    nodes_first_solution=p.nodes_first_solution,
+                    iterations_first_solution=p.iterations_first_solution,
                     states=states[: ne + 1].copy() if p.n_solutions else states[:0].copy(),
                     controls=controls[:ne].copy(), steps=steps[:ne].copy(),
                     history_time_s=ht[:ns].copy(), history_cost=hc[:ns].copy(), history_iteration=hi[:ns].copy())
@@ -355,6 +359,12 @@ class Planner:
         t.parents, t.steps = parents.ctypes.data_as(_PI32), steps.ctypes.data_as(_PI32)
         xg = _f32(x_goal)
         return _check(lib().pakr_tree_import(self.h, C.byref(t), _pf(xg)), "pakr_tree_import")
+
+    def tree_size(self):
+        """(node count, expansion counter) of the tree."""
+        n, it = C.c_int64(0), C.c_uint32(0)
+        _check(lib().pakr_tree_size(self.h, C.byref(n), C.byref(it)), "pakr_tree_size")
+        return int(n.value), int(it.value)
 
     def tree_truncate(self, count):
         return _check(lib().pakr_tree_truncate(self.h, int(count)), "pakr_tree_truncate")

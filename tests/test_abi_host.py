@@ -111,3 +111,35 @@ def test_binding_refuses_missing_library(monkeypatch, tmp_path):
     monkeypatch.setattr(pakr, "_LIB_PATH", str(tmp_path / "libpakr.so"))
     with pytest.raises(RuntimeError, match="missing"):
         pakr.lib()
+
+
+STRUCTS = {"pakr_problem_desc": pakr.ProblemDesc, "pakr_expand_info": pakr.ExpandInfo,
+           "pakr_tree_host": pakr.TreeHost, "pakr_path": pakr.Path, "pakr_traj_params": pakr.TrajParams,
+           "pakr_batch_query": pakr.BatchQuery, "pakr_batch_tuning": pakr.BatchTuning,
+           "pakr_batch_result": pakr.BatchResult}
+
+
+def test_binding_structs_match_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets the
+    C compiler gives the header's struct (a small C program prints them)."""
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pakr.h"', "int main(void) {"]
+    for cname, py in STRUCTS.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    exe = tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    import subprocess
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            c, f, v = ln.split()
+            got[(c, f)] = int(v)
+    for cname, py in STRUCTS.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)

@@ -28,6 +28,8 @@ def check_path_properties(spec, res):
     assert np.all((res["steps"] >= spec["s_min"]) & (res["steps"] <= spec["s_max"]))
     assert np.all((res["controls"] >= spec["u_lo"]) & (res["controls"] <= spec["u_hi"]))
     hc = res["history_cost"]
+    assert res["iterations_first_solution"] == res["history_iteration"][0] + 1
+    assert res["nodes_first_solution"] > 1
     assert np.all(np.diff(hc) < 0), hc
     assert abs(hc[-1] - res["cost"]) <= 1e-6 * max(1, res["cost"])
     # path-length cost is at least the straight-line distance start -> goal ball
@@ -98,4 +100,38 @@ def test_plan_quadrotor_runs(cuda_lib):
     r = planner.plan(spec["x_init"], spec["x_goal"], budget_s=2.0, seed=0)
     assert r["iterations"] > 0
     check_path_properties(spec, r)
+    planner.close()
+
+
+def test_tree_size_matches_export(cuda_lib):
+    spec = W.problem("di2", env_seed=0)
+    planner = pakr.Planner(spec)
+    planner.plan(spec["x_init"], spec["x_goal"], budget_s=60.0, max_iterations=15, seed=4)
+    n, it = planner.tree_size()
+    tree = planner.tree_export()
+    assert n == len(tree["parents"]) and n >= 1
+    assert it == tree["iteration"]
+    planner.close()
+
+
+@pytest.mark.parametrize("B,A", [(4096, 2), (4096, 128)])
+def test_quadrotor_table4_shapes(cuda_lib, B, A):
+    """The batch size x branching factor shapes of Table 4 (K = B / A parents)
+    run on the 12D quadrotor: the tree grows by at most B nodes per expansion
+    and any path found has the properties of a solution."""
+    spec = W.with_sizes(W.problem("quad12", env_seed=0), K=B // A, k=A, cap=200000)
+    planner = pakr.Planner(spec)
+    iters = 6
+    r = planner.plan(spec["x_init"], spec["x_goal"], budget_s=60.0, max_iterations=iters, seed=1,
+                     stop_at_first=True)
+    n, _ = planner.tree_size()
+    assert 1 < n <= 1 + r["iterations"] * B
+    assert r["iterations"] <= iters
+    if r["n_solutions"]:
+        assert 1 < r["nodes_first_solution"] <= 1 + r["iterations_first_solution"] * B
+        assert r["iterations_first_solution"] == r["iterations"]
+        pd = spec["pdim"]
+        s = r["states"]
+        assert np.allclose(s[0], spec["x_init"])
+        assert np.linalg.norm(s[-1][:pd] - spec["x_goal"][:pd]) <= spec["goal_r"] * (1 + 1e-5)
     planner.close()
