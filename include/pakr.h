@@ -83,6 +83,15 @@ typedef enum pakr_heuristic {
 } pakr_heuristic;
 
 /* Per-rollout outcome of the last expansion (pakr_debug_last_expand). */
+/* Nearest-neighbour kernel choice.  Both give the same result (the exact FP32
+ * argmin, lowest index on a tie).  The tensor-core kernel needs a packed
+ * operand copy of the tree (4 * (3d + 2 rounded up to 8) bytes per node). */
+typedef enum pakr_nn_mode {
+    PAKR_NN_AUTO = 0,           /* tensor cores for trees of >= 65536 nodes when n_parents >= 256, FP32 otherwise */
+    PAKR_NN_FP32 = 1,           /* FP32 kernel only; no packed copy is kept */
+    PAKR_NN_TENSOR = 2          /* tensor-core kernel at every tree size */
+} pakr_nn_mode;
+
 typedef enum pakr_outcome {
     PAKR_ROLLOUT_APPENDED = 0,  /* inserted into the tree */
     PAKR_ROLLOUT_PRUNED = 1,    /* f-cost not below the bound */
@@ -119,6 +128,7 @@ typedef struct pakr_problem_desc {
     uint64_t workspace_bytes;   /* size of workspace; see pakr_workspace_size */
     int32_t path_cap;           /* maximum solution path length in edges kept on the device; 0 = 4096 */
     int32_t history_cap;        /* maximum AO-x solutions recorded per plan; 0 = 1024 */
+    int32_t nn_mode;            /* pakr_nn_mode */
 } pakr_problem_desc;
 
 typedef struct pakr_planner pakr_planner;

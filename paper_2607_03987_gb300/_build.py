@@ -11,8 +11,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libpakr.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["pakr_kernels.cu", "pakr_api.cu", "pakr_static.cu", "pakr_batch.cu", "pakr_traj.cu"]
-HEADERS = ["pakr_internal.h", "pakr_device.cuh"]
+SOURCES = ["pakr_kernels.cu", "pakr_api.cu", "pakr_static.cu", "pakr_batch.cu", "pakr_traj.cu", "pakr_nn_tc.cu"]
+HEADERS = ["pakr_internal.h", "pakr_device.cuh", "pakr_tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no implicit multiply-add contraction, so every kernel that runs a
 # device function rounds it the same way whatever its template parameters (the

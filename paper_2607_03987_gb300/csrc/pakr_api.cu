@@ -72,14 +72,15 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Byte offsets of every device buffer inside one allocation.
 struct Layout {
-    size_t X, U, cost, fcost, parent, steps;
+    size_t X, U, cost, fcost, parent, steps, XT;
     size_t xr, nn_key, st_x, st_u, st_cost, st_f, st_steps, st_parent, outcome, goal, block_count;
     size_t boxes, spheres, ctl, pp;
     size_t path_nodes, path_x, path_u, path_steps, hist_t, hist_cost, hist_iter;
     size_t total;
 };
 
-Layout make_layout(const DimInfo &di, int64_t cap, int K, int k, int nb, int ns, int path_cap, int hist_cap)
+Layout make_layout(const DimInfo &di, int64_t cap, int K, int k, int nb, int ns, int path_cap, int hist_cap,
+                   int tc_row_floats)
 {
     Layout L{};
     size_t off = 0;
@@ -94,9 +95,11 @@ Layout make_layout(const DimInfo &di, int64_t cap, int K, int k, int nb, int ns,
     L.X = take(sizeof(float) * di.d * c);
     L.U = take(sizeof(float) * di.m * c);
     L.cost = take(sizeof(float) * c);
-    L.fcost = take(sizeof(float) * c);
+    L.fcost = take(sizeof(float) * (c + 4));  // bulk copies of f-costs round up to 16 bytes
     L.parent = take(sizeof(int) * c);
     L.steps = take(sizeof(int) * c);
+    // packed tensor-core operand rows, whole 256-node tiles
+    L.XT = take(tc_row_floats > 0 ? sizeof(float) * (size_t)tc_row_floats * ((c + 255) / 256 * 256) : 0);
     L.xr = take(sizeof(float) * di.d * (size_t)K);
     L.nn_key = take(sizeof(unsigned long long) * (size_t)K);
     L.st_x = take(sizeof(float) * di.d * R);
@@ -189,7 +192,27 @@ pakr_status check_desc(const pakr_problem_desc *d, DimInfo *di)
         return fail(PAKR_ERR_INVALID_ARG, "tree_cap must be in [1, 2^31-1]");
     if (d->path_cap < 0 || d->history_cap < 0)
         return fail(PAKR_ERR_INVALID_ARG, "path_cap / history_cap must be >= 0");
+    if (d->nn_mode < PAKR_NN_AUTO || d->nn_mode > PAKR_NN_TENSOR)
+        return fail(PAKR_ERR_INVALID_ARG, "nn_mode %d is not a pakr_nn_mode", d->nn_mode);
     return PAKR_OK;
+}
+
+// Smallest tree size the tensor-core nearest neighbour takes (0x7FFFFFFF: never), and
+// the floats per packed node row it needs (0: no packed copy).  Below about 64k nodes, or
+// with fewer than two query blocks, the FP32 kernel is faster.
+constexpr int kTcAutoMinNodes = 65536;
+constexpr int kTcAutoMinQueries = 256;
+int tc_min_nodes(const pakr_problem_desc *d)
+{
+    if (d->nn_mode == PAKR_NN_TENSOR)
+        return 0;
+    if (d->nn_mode == PAKR_NN_AUTO && d->n_parents >= kTcAutoMinQueries)
+        return kTcAutoMinNodes;
+    return 0x7FFFFFFF;
+}
+int tc_floats(const pakr_problem_desc *d, const DimInfo &di)
+{
+    return tc_min_nodes(d) < 0x7FFFFFFF ? tc_operand_floats(di.d) : 0;
 }
 
 struct EventPair {
@@ -420,7 +443,7 @@ pakr_status pakr_workspace_size(const pakr_problem_desc *desc, uint64_t *bytes_o
     const int pc = desc->path_cap ? desc->path_cap : 4096;
     const int hc = desc->history_cap ? desc->history_cap : 1024;
     Layout L = make_layout(di, desc->tree_cap, desc->n_parents, desc->branching, desc->n_boxes, desc->n_spheres, pc,
-                           hc);
+                           hc, tc_floats(desc, di));
     *bytes_out = L.total + 256;  // slack for aligning the caller's base pointer
     return PAKR_OK;
 }
@@ -449,7 +472,8 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
     p->k = desc->branching;
     p->path_cap = desc->path_cap ? desc->path_cap : 4096;
     p->hist_cap = desc->history_cap ? desc->history_cap : 1024;
-    p->lay = make_layout(di, p->cap, p->K, p->k, desc->n_boxes, desc->n_spheres, p->path_cap, p->hist_cap);
+    p->lay = make_layout(di, p->cap, p->K, p->k, desc->n_boxes, desc->n_spheres, p->path_cap, p->hist_cap,
+                         tc_floats(desc, di));
 
     auto cleanup = [&](pakr_status s) {
         pakr_destroy(p);
@@ -482,7 +506,8 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
     char *b = p->base;
     const Layout &L = p->lay;
     p->T = DevTree{(float *)(b + L.X), (float *)(b + L.U), (float *)(b + L.cost), (float *)(b + L.fcost),
-                   (int *)(b + L.parent), (int *)(b + L.steps)};
+                   (int *)(b + L.parent), (int *)(b + L.steps),
+                   tc_floats(desc, di) > 0 ? (float *)(b + L.XT) : nullptr};
     p->W = DevWork{(float *)(b + L.xr),       (unsigned long long *)(b + L.nn_key),
                    (float *)(b + L.st_x),     (float *)(b + L.st_u),
                    (float *)(b + L.st_cost),  (float *)(b + L.st_f),
@@ -526,6 +551,24 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
     P.K = desc->n_parents;
     P.k = desc->branching;
     P.cap = (int)desc->tree_cap;
+    // tensor-core filter: centre and radius of the weighted state box (rounded up)
+    {
+        double r2 = 0.0;
+        for (int a = 0; a < kMaxD; ++a) {
+            P.tc_c[a] = a < di.d ? 0.5f * (desc->x_lo[a] + desc->x_hi[a]) * P.sw[a] : 0.f;
+            if (a < di.d) {
+                const double h = 0.5 * ((double)desc->x_hi[a] - (double)desc->x_lo[a]) * P.sw[a];
+                r2 += h * h;
+            }
+        }
+        P.tc_xbox2 = (float)(r2 * 1.0001 + 1e-30);
+        P.tc_min_n = p->T.XT ? tc_min_nodes(desc) : 0x7FFFFFFF;
+        if (p->T.XT) {
+            e = tc_configure(P);
+            if (e != cudaSuccess)
+                return cleanup(fail(PAKR_ERR_CUDA, "tensor-core kernel setup failed: %s", cudaGetErrorString(e)));
+        }
+    }
 
     // Obstacles as padded float4 records.
     std::vector<float4> box4(2 * (size_t)desc->n_boxes), sph4((size_t)desc->n_spheres);
@@ -576,6 +619,18 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
     C.nn_qgroups = (p->K + per_block - 1) / per_block;
     const int occ = std::max(1, nn_blocks_per_sm(di.d, C.nn_variant));
     C.nn_chunks = std::max(1, sms * occ / C.nn_qgroups);
+    // tensor-core grid: one CTA per SM; node chunks x query blocks in near-full waves of the SMs
+    C.tc_qblocks = (p->K + 127) / 128;  // 128 queries per tensor-core CTA
+    C.tc_chunks = std::max(1, sms / C.tc_qblocks);
+    for (int w = 1; w <= 16; ++w) {
+        const int c = (w * sms + C.tc_qblocks - 1) / C.tc_qblocks;
+        const int items = c * C.tc_qblocks;
+        const int waves = (items + sms - 1) / sms;
+        if ((double)items / ((double)waves * sms) >= 0.95) {
+            C.tc_chunks = c;
+            break;
+        }
+    }
     const int64_t R = (int64_t)p->K * p->k;
     // Lanes per rollout: enough threads for about one resident wave on every
     // SM, but no more lanes than there are obstacles to split between them.

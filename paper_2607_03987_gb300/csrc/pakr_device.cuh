@@ -10,6 +10,7 @@
 #include <stdint.h>
 
 #include "pakr_internal.h"
+#include "pakr_tc.cuh"
 
 namespace pakr {
 
@@ -298,6 +299,18 @@ __device__ __forceinline__ void begin_batch(Ctl *ctl, float bound)
     ctl->n_no_parent = 0;
     ctl->n_dropped = 0;
 }
+
+// Instantiate BODY for the runtime dynamics id (DYN_ names the model).
+#define PAKR_DISPATCH_DYN(dyn, BODY)                                                                                   \
+    switch (dyn) {                                                                                                     \
+    case DI2: { constexpr int DYN_ = DI2; BODY; } break;                                                               \
+    case DI3: { constexpr int DYN_ = DI3; BODY; } break;                                                               \
+    case QUAD12: { constexpr int DYN_ = QUAD12; BODY; } break;                                                         \
+    case DUBINS3D: { constexpr int DYN_ = DUBINS3D; BODY; } break;                                                     \
+    case UNICYCLE1: { constexpr int DYN_ = UNICYCLE1; BODY; } break;                                                   \
+    case UNICYCLE2: { constexpr int DYN_ = UNICYCLE2; BODY; } break;                                                   \
+    default: return cudaErrorInvalidValue;                                                                             \
+    }
 
 // ---------------------------------------------------------------------------
 // k_nn: cost-pruned brute-force nearest neighbour.
@@ -830,9 +843,13 @@ __device__ __forceinline__ void append_block(const DevProblem &P, Ctl *ctl, cons
     if (cand) {
         if (pos < cap) {
             const int p = (int)pos;
+            float xs[D];
 #pragma unroll
-            for (int a = 0; a < D; ++a)
-                T.X[(size_t)a * cap + p] = W.st_x[(size_t)a * R + r];
+            for (int a = 0; a < D; ++a) {
+                xs[a] = W.st_x[(size_t)a * R + r];
+                T.X[(size_t)a * cap + p] = xs[a];
+            }
+            tc_pack_node<D>(P, T, ctl, p, xs);
 #pragma unroll
             for (int a = 0; a < M; ++a)
                 T.U[(size_t)a * cap + p] = W.st_u[(size_t)a * R + r];
@@ -985,6 +1002,8 @@ __device__ __forceinline__ bool aox_init_one(const DevProblem &P, Ctl *ctl, cons
     T.fcost[0] = heuristic<D, PD>(x, P, goal);
     T.parent[0] = -1;
     T.steps[0] = 0;
+    ctl->tc_flag = 0u;
+    tc_pack_node<D>(P, T, ctl, 0, x);
     ctl->count = 1;
     ctl->iteration = 0u;
     ctl->seed = seed;

@@ -18,7 +18,7 @@ enum Outcome { OUT_APPENDED = 0, OUT_PRUNED = 1, OUT_COLLIDED = 2, OUT_NO_PARENT
 enum { COST_PATH_LENGTH = 0, COST_DURATION = 1 };
 enum { H_POSITION = 0, H_FULLSTATE = 1 };
 enum { MODE_EXPAND = 0, MODE_PLAN = 1 };
-enum { ERR_PATH_CYCLE = 1, ERR_BAD_PARENT = 2 };
+enum { ERR_PATH_CYCLE = 1, ERR_BAD_PARENT = 2, ERR_TC_TIMEOUT = 4 };
 
 // Problem constants, passed to every kernel by value.
 struct DevProblem {
@@ -35,6 +35,11 @@ struct DevProblem {
     int cost, heuristic;
     int K, k;             // parents per iteration, controls per parent
     int cap;              // tree capacity
+    // tensor-core nearest neighbour: centre of the weighted state box, bound on |x_w - c|^2,
+    // smallest tree size that takes the tensor-core kernel (INT_MAX: never)
+    float tc_c[kMaxD];
+    float tc_xbox2;
+    int tc_min_n = 0x7FFFFFFF;
 };
 
 // Dimension-major tree arrays.
@@ -45,6 +50,7 @@ struct DevTree {
     float *fcost;   // cap, cost + h(x)
     int *parent;    // cap
     int *steps;     // cap
+    float *XT = nullptr;  // packed tensor-core operand rows, 256-node tiles (nullptr: not kept)
 };
 
 // Per-batch workspace.
@@ -73,7 +79,7 @@ struct Ctl {
     int n_appended, n_pruned, n_collided, n_no_parent, n_dropped;
     int err;
     int status;              // tree_reset: 1 valid root, 0 invalid
-    int pad0;
+    unsigned tc_flag;        // a tree node lies outside the box bound of the tensor-core filter
     float x_goal[kMaxD];
     // AO-x plan state
     float c_best;
@@ -120,6 +126,7 @@ struct LaunchCfg {
     int prop_lanes;     // lanes per rollout in k_propagate (1, 2, 4 or 8); k_append takes prop_threads / prop_lanes
     int sample_threads, sample_blocks;
     int obs_smem_bytes; // shared memory for obstacles + goal
+    int tc_chunks, tc_qblocks;  // tensor-core nearest neighbour grid (node chunks x query blocks)
 };
 
 // Kernel launchers (pakr_kernels.cu).  Each returns the launch error.
@@ -127,6 +134,11 @@ cudaError_t launch_sample(const DevProblem &P, Ctl *ctl, const DevWork &W, const
                           unsigned long long seed, int mode, cudaStream_t s);
 cudaError_t launch_nn(const DevProblem &P, const Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
                       cudaStream_t s);
+cudaError_t launch_nn_tc(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
+                         cudaStream_t s);
+cudaError_t launch_tc_pack(const DevProblem &P, Ctl *ctl, const DevTree &T, int count, cudaStream_t s);
+int tc_operand_floats(int d);  // floats per packed node row (3d + 2 rounded up to 8)
+cudaError_t tc_configure(const DevProblem &P);
 cudaError_t launch_propagate(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
                              cudaStream_t s);
 cudaError_t launch_append(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,

@@ -42,6 +42,8 @@ __global__ void __launch_bounds__(NT, (NnMinBlocks<D, NT>::value))
     constexpr int RW = (2 * D + 2 + 3) / 4 * 4;
     __shared__ __align__(16) float s_node[TILE * RW];
     const int n = ctl->n_start;
+    if (n >= P.tc_min_n)
+        return;  // large trees take k_nn_tc
     const int per = nn_chunk_nodes<G>(n, gridDim.x);
     const int start = blockIdx.x * per;
     const int end = min(n, start + per);
@@ -86,6 +88,8 @@ __global__ void k_tree_reset(DevProblem P, Ctl *ctl, DevTree T, const float *x_i
     T.fcost[0] = heuristic<D, PD>(x, P, goal);
     T.parent[0] = -1;
     T.steps[0] = 0;
+    ctl->tc_flag = 0u;
+    tc_pack_node<D>(P, T, ctl, 0, x);
     ctl->count = 1;
     ctl->iteration = 0u;
     ctl->err = 0;
@@ -106,6 +110,7 @@ __global__ void k_import_fcost(DevProblem P, Ctl *ctl, DevTree T, int count)
         goal[a] = ctl->x_goal[a];
     }
     T.fcost[j] = T.cost[j] + heuristic<D, PD>(x, P, goal);
+    tc_pack_node<D>(P, T, ctl, j, x);
 }
 
 // Fresh AO-x run: goal, root, c_best = +inf, clock start.  Closes the while
@@ -156,17 +161,6 @@ __global__ void k_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t
 // ---------------------------------------------------------------------------
 // Launchers and dispatch.
 // ---------------------------------------------------------------------------
-#define PAKR_DISPATCH_DYN(dyn, BODY)                                                                                   \
-    switch (dyn) {                                                                                                     \
-    case DI2: { constexpr int DYN_ = DI2; BODY; } break;                                                               \
-    case DI3: { constexpr int DYN_ = DI3; BODY; } break;                                                               \
-    case QUAD12: { constexpr int DYN_ = QUAD12; BODY; } break;                                                         \
-    case DUBINS3D: { constexpr int DYN_ = DUBINS3D; BODY; } break;                                                     \
-    case UNICYCLE1: { constexpr int DYN_ = UNICYCLE1; BODY; } break;                                                   \
-    case UNICYCLE2: { constexpr int DYN_ = UNICYCLE2; BODY; } break;                                                   \
-    default: return cudaErrorInvalidValue;                                                                             \
-    }
-
 constexpr int kNnTile = 256;
 constexpr int kNnGroup = 8;
 
@@ -191,11 +185,21 @@ static cudaError_t launch_nn_d(const DevProblem &P, const Ctl *ctl, const DevTre
     return cudaGetLastError();
 }
 
+// Both nearest-neighbour kernels are launched when the tree keeps the packed
+// operand copy; each returns at once unless the device-side tree size is in its
+// range (k_nn below P.tc_min_n, k_nn_tc from it), so no host read is needed.
 cudaError_t launch_nn(const DevProblem &P, const Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
                       cudaStream_t s)
 {
-    PAKR_DISPATCH_DYN(P.dyn, return launch_nn_d<Dims<DYN_>::D>(P, ctl, T, W, L, s));
-    return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (P.tc_min_n > 0) {
+        PAKR_DISPATCH_DYN(P.dyn, e = launch_nn_d<Dims<DYN_>::D>(P, ctl, T, W, L, s));
+        if (e != cudaSuccess)
+            return e;
+    }
+    if (T.XT && P.tc_min_n < 0x7FFFFFFF)
+        e = launch_nn_tc(P, const_cast<Ctl *>(ctl), T, W, L, s);
+    return e;
 }
 
 template <int DYN>

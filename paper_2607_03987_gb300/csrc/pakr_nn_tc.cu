@@ -1,0 +1,482 @@
+// k_nn_tc: cost-pruned nearest neighbour on the tensor cores (tcgen05, TF32 hi/lo split).
+//
+// Same result as k_nn (Algorithm 1 NearestNeighbor over the frozen snapshot,
+// Sec. IV-A, IV-B): for each query the eligible node (f-cost below the bound)
+// with the smallest exact FP32 squared distance, the lowest index on a tie.
+//
+// A CTA takes 128 queries (one query block) and a chunk of whole 256-node tiles.
+// Per tile the tensor cores compute the filter a = |x - c|^2 - 2 (q - c).(x - c)
+// for all 128 x 256 pairs into TMEM; reader warps take each row's minimum over
+// groups of 16 nodes and remember the groups whose minimum lies within `band`
+// of the row's running minimum (band = 2 * B, B the bound of tc_bound_coef on
+// |a + |q - c|^2 - e|).  After the chunk, every node whose exact distance could
+// be the row's minimum lies in a remembered group (its filter value is at most
+// m1 + band), so recomputing e on those groups gives the exact argmin.  A row
+// whose candidate ring overflowed, or a tree flagged as leaving the box bound,
+// is rescanned exactly by the whole CTA.  Chunk results merge with a 64-bit
+// atomicMin of (distance bits << 32 | index), as in k_nn.
+//
+// Roles (14 warps, one CTA per SM: it allocates all 512 TMEM columns):
+//   warp 0 lane 0   bulk-copies packed node tiles (T.XT) and f-costs into a ring of stages;
+//   warps 1-4       mask ineligible rows (|x|^2 columns := 2^100), wait for the accumulator
+//                   the tile will use to be released, then signal "tile ready";
+//   warp 5 lane 0   waits "tile ready" and issues KT/8 MMAs (M 128, N 256, K 8) per tile;
+//   warps 6-13      read the accumulators (tcgen05.ld), group minima, candidate rings.
+// Every wait is bounded (1 s of device time); on timeout the CTA sets ERR_TC_TIMEOUT,
+// stops issuing work and still frees its TMEM.
+#include "pakr_device.cuh"
+#include "pakr_tc.cuh"
+
+namespace pakr {
+
+template <int D>
+__device__ __forceinline__ float tc_exact(const DevProblem &P, const DevTree &T, int j, float bound, const float *qv)
+{
+    const float f = T.fcost[j];
+    float acc = 0.f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const float diff = __fadd_rn(qv[a], -(T.X[(size_t)a * P.cap + j] * P.sw[a]));
+        acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
+    }
+    return (f < bound) ? acc : __int_as_float(0x7f800000);
+}
+
+// grid (chunks, ceil(K / 128)), kTcThreads threads, TcShape<D>::SMEM_REQ dynamic shared memory.
+// T.fcost must be readable 4 floats past the node count (the f-cost copy rounds up to 16 bytes).
+template <int D>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_nn_tc(DevProblem P, Ctl *__restrict__ ctl, DevTree T, DevWork W)
+{
+    using S = TcShape<D>;
+    constexpr int KT = S::KT;
+    constexpr int NST = S::NSTAGE;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char *sA = tc_smem;
+    unsigned char *sB0 = tc_smem + S::A_BYTES;
+    float *sF0 = reinterpret_cast<float *>(tc_smem + S::A_BYTES + NST * S::TILE_BYTES);
+    float *ring_val = reinterpret_cast<float *>(tc_smem + S::A_BYTES + NST * (S::TILE_BYTES + S::F_BYTES));
+    int *ring_grp = reinterpret_cast<int *>(ring_val + kTcRing * kTcReaders);
+    __shared__ __align__(8) unsigned long long s_loaded[NST], s_full[NST], s_free[NST];
+    __shared__ __align__(8) unsigned long long s_done[kTcAcc], s_empty[kTcAcc];
+    __shared__ uint32_t s_tbase;
+    __shared__ volatile int s_abort;
+    __shared__ float s_m1[kTcM];
+    __shared__ int s_pos[kTcM], s_ovf[kTcM];
+    __shared__ int s_nflag, s_flag_qid[kTcM];
+    __shared__ float s_flag_q[kTcM][D];
+
+    const int n = ctl->n_start;
+    if (n < P.tc_min_n)
+        return;  // small trees take k_nn
+    const int ntile_all = (n + kTcN - 1) / kTcN;
+    const int tiles_per = (ntile_all + gridDim.x - 1) / gridDim.x;
+    const int tile0 = blockIdx.x * tiles_per;
+    const int ntiles = min(ntile_all, tile0 + tiles_per) - tile0;
+    if (ntiles <= 0)
+        return;
+    const int start = tile0 * kTcN;
+    const int end = min(n, start + ntiles * kTcN);
+    const float bound = ctl->bound;
+    const bool flagged = ctl->tc_flag != 0;
+    const int K = P.K;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int qbase = blockIdx.y * kTcM;
+    const unsigned long long kWaitNs = 1000000000ull;
+
+    // ---- setup: TMEM, barriers, the query operand ----
+    if (warp == kTcMmaWarp) {
+        tmem_alloc(smem_u32(&s_tbase), 512);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < NST; ++i) {
+            mbar_init(smem_u32(&s_loaded[i]), 1);
+            mbar_init(smem_u32(&s_full[i]), 4);
+            mbar_init(smem_u32(&s_free[i]), 1);
+        }
+#pragma unroll
+        for (int i = 0; i < kTcAcc; ++i) {
+            mbar_init(smem_u32(&s_done[i]), 1);
+            mbar_init(smem_u32(&s_empty[i]), kTcReaders / 32);
+        }
+        fence_mbar_init();
+        s_abort = 0;
+        s_nflag = 0;
+    }
+    if (tid < kTcM) {
+        // query row: -2 (q - c) split as hi (against x_hi), hi (against x_lo), lo (against x_hi); 1, 1
+        const int q = qbase + tid;
+        float row[KT];
+#pragma unroll
+        for (int k = 0; k < KT; ++k)
+            row[k] = 0.f;
+        if (q < K) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const float v = -2.f * (W.xr[(size_t)a * K + q] * P.sw[a] - P.tc_c[a]);
+                const float hi = tf32_trunc(v);
+                row[a] = hi;
+                row[D + a] = hi;
+                row[2 * D + a] = tf32_trunc(v - hi);
+            }
+            row[3 * D] = 1.f;
+            row[3 * D + 1] = 1.f;
+        }
+#pragma unroll
+        for (int c = 0; c < KT / 4; ++c)
+            *reinterpret_cast<float4 *>(sA + tc_off<D>(tid, 4 * c)) =
+                make_float4(row[4 * c], row[4 * c + 1], row[4 * c + 2], row[4 * c + 3]);
+        fence_async_smem();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = s_tbase;
+
+    // reader state
+    const int e = tid - kTcReader0 * 32;
+    const int quarter = warp & 3, half = (warp - kTcReader0) >> 2;
+    const int qrow = 32 * quarter + lane;
+    const int qid = qbase + qrow;
+    float qv[D];
+    float m1 = kTcEligible;
+    int pos = 0, ovf = 0;
+    float band = 0.f;
+
+    if (flagged) {
+        // the tree has a node outside the box bound: no filter; the block rescans exactly below
+    } else if (warp == kTcLoadWarp) {
+        if (lane == 0) {
+            const uint32_t sB = smem_u32(sB0), sF = smem_u32(sF0);
+            for (int t = 0; t < ntiles && !s_abort; ++t) {
+                const int b = t % NST;
+                if (t >= NST && !mbar_wait_bounded(smem_u32(&s_free[b]), ((t - NST) / NST) & 1, kWaitNs)) {
+                    s_abort = 1;
+                    atomicOr(&ctl->err, ERR_TC_TIMEOUT);
+                    break;
+                }
+                const int j0 = start + t * kTcN;
+                const uint32_t fbytes = (uint32_t)(((min(kTcN, end - j0) + 3) & ~3) * 4);
+                const uint32_t bar = smem_u32(&s_loaded[b]);
+                mbar_arrive_expect_tx(bar, (uint32_t)S::TILE_BYTES + fbytes);
+                bulk_g2s(sB + b * S::TILE_BYTES,
+                         reinterpret_cast<const unsigned char *>(T.XT) + (size_t)(tile0 + t) * S::TILE_BYTES,
+                         S::TILE_BYTES, bar);
+                bulk_g2s(sF + b * S::F_BYTES, T.fcost + j0, fbytes, bar);
+            }
+        }
+        __syncwarp();
+    } else if (warp >= kTcPatch0 && warp < kTcPatch0 + 4) {
+        const int r0 = tid - kTcPatch0 * 32;  // rows r0 and r0 + 128 of every tile
+        for (int t = 0; t < ntiles; ++t) {
+            const int b = t % NST;
+            const bool ok = !s_abort && mbar_wait_bounded(smem_u32(&s_loaded[b]), (t / NST) & 1, kWaitNs);
+            if (!ok && !s_abort) {
+                s_abort = 1;
+                atomicOr(&ctl->err, ERR_TC_TIMEOUT);
+            }
+            if (ok) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = r0 + 128 * h;
+                    const int j = start + t * kTcN + r;
+                    if (!(j < end && sF0[b * kTcN + r] < bound)) {
+                        unsigned char *rowp = sB0 + b * S::TILE_BYTES;
+                        *reinterpret_cast<float *>(rowp + tc_off<D>(r, 3 * D)) = kTcSentinel;
+                        *reinterpret_cast<float *>(rowp + tc_off<D>(r, 3 * D + 1)) = 0.f;
+                    }
+                }
+                fence_async_smem();
+            }
+            __syncwarp();
+            if (lane == 0) {
+                // "tile ready" also means the accumulator it will use (tile t - 2's) has been read
+                if (ok && t >= kTcAcc && !s_abort &&
+                    !mbar_wait_bounded(smem_u32(&s_empty[t % kTcAcc]), ((t - kTcAcc) / kTcAcc) & 1, kWaitNs)) {
+                    s_abort = 1;
+                    atomicOr(&ctl->err, ERR_TC_TIMEOUT);
+                }
+                mbar_arrive(smem_u32(&s_full[b]));
+            }
+        }
+    } else if (warp == kTcMmaWarp) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tf32(kTcM, kTcN);
+            const uint32_t a_addr = smem_u32(sA), b_addr = smem_u32(sB0);
+            for (int t = 0; t < ntiles && !s_abort; ++t) {
+                const int st = t % NST, ac = t % kTcAcc;
+                if (!mbar_wait_bounded(smem_u32(&s_full[st]), (t / NST) & 1, kWaitNs)) {
+                    s_abort = 1;
+                    atomicOr(&ctl->err, ERR_TC_TIMEOUT);
+                    break;
+                }
+                if (s_abort)
+                    break;
+                tc_fence_after();
+#pragma unroll
+                for (int s = 0; s < KT / 8; ++s)
+                    mma_tf32_ss(tbase + (uint32_t)(ac * kTcN), smem_desc(a_addr + 2 * S::LBO * s, S::LBO, S::SBO),
+                                smem_desc(b_addr + st * S::TILE_BYTES + 2 * S::LBO * s, S::LBO, S::SBO), idesc,
+                                s > 0 ? 1u : 0u);
+                mma_commit(smem_u32(&s_free[st]));
+                mma_commit(smem_u32(&s_done[ac]));
+            }
+        }
+        __syncwarp();
+    } else if (warp >= kTcReader0) {
+        float qc2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            qv[a] = (qid < K) ? W.xr[(size_t)a * K + qid] * P.sw[a] : 0.f;
+            const float d = qv[a] - P.tc_c[a];
+            qc2 = __fmaf_rn(d, d, qc2);
+        }
+        const float Rq = sqrtf(qc2) * 1.0001f + sqrtf(P.tc_xbox2);
+        band = 2.f * tc_bound_coef<D>() * Rq * Rq;
+        float thr = kTcEligible;
+        for (int t = 0; t < ntiles; ++t) {
+            if (__any_sync(0xFFFFFFFFu, s_abort != 0))
+                break;
+            const int b = t % kTcAcc;
+            const bool ok =
+                __all_sync(0xFFFFFFFFu, mbar_wait_bounded(smem_u32(&s_done[b]), (t / kTcAcc) & 1, kWaitNs));
+            if (!ok) {
+                if (lane == 0) {
+                    s_abort = 1;
+                    atomicOr(&ctl->err, ERR_TC_TIMEOUT);
+                }
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tcol = tbase + (uint32_t)(b * kTcN + 128 * half) + ((uint32_t)(32 * quarter) << 16);
+            const int gbase = start + t * kTcN + 128 * half;
+#pragma unroll 1
+            for (int c = 0; c < 2; ++c) {
+                float v[64];
+                __syncwarp();
+                tmem_ld64(tcol + 64 * c, v);
+                if (c == 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0)
+                        mbar_arrive(smem_u32(&s_empty[b]));
+                }
+                float m[4];
+#pragma unroll
+                for (int h4 = 0; h4 < 4; ++h4)
+                    m[h4] = min16(v + 16 * h4);
+#pragma unroll
+                for (int h4 = 0; h4 < 4; ++h4) {
+                    if (m[h4] <= thr) {
+                        if (m[h4] < m1) {
+                            m1 = m[h4];
+                            thr = m1 + band;
+                        }
+                        const int slot = pos & (kTcRing - 1);
+                        // an entry still within the band would be lost: the row falls back to a rescan
+                        if (pos >= kTcRing && ring_val[slot * kTcReaders + e] <= thr)
+                            ovf = 1;
+                        const int g0 = gbase + 64 * c + 16 * h4;
+                        ring_val[slot * kTcReaders + e] = m[h4];
+                        ring_grp[slot * kTcReaders + e] = g0;
+                        ++pos;
+#pragma unroll
+                        for (int a = 0; a < D; ++a)
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(T.X + (size_t)a * P.cap + g0));
+                    }
+                }
+            }
+        }
+        if (half == 1) {
+            s_m1[qrow] = m1;
+            s_pos[qrow] = pos;
+            s_ovf[qrow] = ovf;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kTcMmaWarp) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 512);
+    }
+    if (s_abort)
+        return;
+
+    // ---- exact resolve of the candidate groups (both column halves of the row) ----
+    if (!flagged && warp >= kTcReader0 && half == 0 && qid < K) {
+        const float m1f = fminf(m1, s_m1[qrow]);
+        if (m1f < kTcEligible) {
+            const float thrf = m1f + band;
+            const bool vec_ok = (P.cap & 3) == 0;  // 16-byte loads need 16-byte aligned rows
+            if (!(ovf || s_ovf[qrow])) {
+                float best = __int_as_float(0x7f800000);
+                int bidx = 0x7FFFFFFF;
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) {
+                    const int owner = e + 128 * h;
+                    const int np = min(h == 0 ? pos : s_pos[qrow], kTcRing);
+#pragma unroll 1
+                    for (int s = 0; s < np; ++s) {
+                        if (!(ring_val[s * kTcReaders + owner] <= thrf))
+                            continue;
+                        const int g0 = ring_grp[s * kTcReaders + owner];
+                        if (vec_ok && g0 + kTcG <= P.cap) {
+#pragma unroll
+                            for (int hb = 0; hb < kTcG; hb += 8) {
+                                float4 xf[D + 1][2];
+#pragma unroll
+                                for (int a = 0; a < D; ++a) {
+                                    const float4 *src =
+                                        reinterpret_cast<const float4 *>(T.X + (size_t)a * P.cap + g0 + hb);
+                                    xf[a][0] = src[0];
+                                    xf[a][1] = src[1];
+                                }
+                                xf[D][0] = reinterpret_cast<const float4 *>(T.fcost + g0 + hb)[0];
+                                xf[D][1] = reinterpret_cast<const float4 *>(T.fcost + g0 + hb)[1];
+#pragma unroll
+                                for (int g = 0; g < 8; ++g) {
+                                    float acc = 0.f;
+#pragma unroll
+                                    for (int a = 0; a < D; ++a) {
+                                        const float4 w = xf[a][g >> 2];
+                                        const float x = (g & 3) == 0 ? w.x : (g & 3) == 1 ? w.y : (g & 3) == 2 ? w.z : w.w;
+                                        const float diff = __fadd_rn(qv[a], -(x * P.sw[a]));
+                                        acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
+                                    }
+                                    const float4 wf = xf[D][g >> 2];
+                                    const float f = (g & 3) == 0 ? wf.x : (g & 3) == 1 ? wf.y : (g & 3) == 2 ? wf.z : wf.w;
+                                    const int j = g0 + hb + g;
+                                    const float ex = (f < bound) ? acc : __int_as_float(0x7f800000);
+                                    if (j < end && (ex < best || (ex == best && j < bidx))) {
+                                        best = ex;
+                                        bidx = j;
+                                    }
+                                }
+                            }
+                        } else {
+#pragma unroll
+                            for (int hb = 0; hb < kTcG; hb += 8) {
+                                float ex[8];
+#pragma unroll
+                                for (int g = 0; g < 8; ++g)  // indices clamped into range so all loads issue together
+                                    ex[g] = tc_exact<D>(P, T, min(g0 + hb + g, end - 1), bound, qv);
+#pragma unroll
+                                for (int g = 0; g < 8; ++g) {
+                                    const int j = g0 + hb + g;
+                                    if (j < end && (ex[g] < best || (ex[g] == best && j < bidx))) {
+                                        best = ex[g];
+                                        bidx = j;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+                if (best < __int_as_float(0x7f800000))
+                    atomicMin(&W.nn_key[qid],
+                              ((unsigned long long)__float_as_uint(best) << 32) | (unsigned long long)(uint32_t)bidx);
+            } else {
+                const int slot = atomicAdd(&s_nflag, 1);
+                s_flag_qid[slot] = qid;
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+                    s_flag_q[slot][a] = qv[a];
+            }
+        }
+    }
+    if (flagged && tid < kTcM) {
+        // every query of the block is rescanned exactly
+        const int q = qbase + tid;
+        if (q < K) {
+            const int slot = atomicAdd(&s_nflag, 1);
+            s_flag_qid[slot] = q;
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                s_flag_q[slot][a] = W.xr[(size_t)a * K + q] * P.sw[a];
+        }
+    }
+    __syncthreads();
+    // exact rescans of the flagged queries by the whole block (coalesced nodes, warp minimum of packed keys)
+    const int nflag = s_nflag;
+    for (int f = 0; f < nflag; ++f) {
+        float q2[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            q2[a] = s_flag_q[f][a];
+        unsigned long long key = kNoKey;
+        for (int j = start + tid; j < end; j += kTcThreads) {
+            const float ed = tc_exact<D>(P, T, j, bound, q2);
+            if (ed < __int_as_float(0x7f800000)) {
+                const unsigned long long k2 =
+                    ((unsigned long long)__float_as_uint(ed) << 32) | (unsigned long long)(uint32_t)j;
+                key = k2 < key ? k2 : key;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, key, o);
+            key = other < key ? other : key;
+        }
+        if (lane == 0 && key != kNoKey)
+            atomicMin(&W.nn_key[s_flag_qid[f]], key);
+    }
+}
+
+template <int D>
+__global__ void k_tc_pack(DevProblem P, Ctl *ctl, DevTree T, int count)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= count)
+        return;
+    float x[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+        x[a] = T.X[(size_t)a * P.cap + j];
+    tc_pack_node<D>(P, T, ctl, j, x);
+}
+
+template <int D>
+static cudaError_t launch_nn_tc_d(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W,
+                                  const LaunchCfg &L, cudaStream_t s)
+{
+    k_nn_tc<D><<<dim3(L.tc_chunks, L.tc_qblocks), kTcThreads, TcShape<D>::SMEM_REQ, s>>>(P, ctl, T, W);
+    return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t tc_configure_d()
+{
+    return cudaFuncSetAttribute(k_nn_tc<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<D>::SMEM_REQ);
+}
+
+// Once per device before the first launch (outside any stream capture): the kernel
+// takes more than 48 KB of dynamic shared memory.
+cudaError_t tc_configure(const DevProblem &P)
+{
+    PAKR_DISPATCH_DYN(P.dyn, return tc_configure_d<Dims<DYN_>::D>());
+    return cudaSuccess;
+}
+
+cudaError_t launch_nn_tc(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
+                         cudaStream_t s)
+{
+    PAKR_DISPATCH_DYN(P.dyn, return launch_nn_tc_d<Dims<DYN_>::D>(P, ctl, T, W, L, s));
+    return cudaSuccess;
+}
+
+cudaError_t launch_tc_pack(const DevProblem &P, Ctl *ctl, const DevTree &T, int count, cudaStream_t s)
+{
+    if (!T.XT || count <= 0)
+        return cudaSuccess;
+    PAKR_DISPATCH_DYN(P.dyn, (k_tc_pack<Dims<DYN_>::D><<<(count + 255) / 256, 256, 0, s>>>(P, ctl, T, count)));
+    return cudaGetLastError();
+}
+
+int tc_operand_floats(int d)
+{
+    return ((3 * d + 2) + 7) / 8 * 8;
+}
+
+}  // namespace pakr

@@ -1,0 +1,267 @@
+// Tensor-core nearest-neighbour support: inline PTX for tcgen05 / TMA / mbarrier,
+// the packed node operand layout, and the error bound of the tensor-core filter.
+//
+// The filter computes, for every (query q, node x) pair,
+//     a = |x - c|^2 - 2 (q - c) . (x - c)
+// with c the centre of the weighted state box.  a + |q - c|^2 is the squared
+// distance, so within one query a orders nodes like the distance.  Operands are
+// FP32 values split into TF32 parts v = hi + lo (hi = v with the low 13
+// mantissa bits cleared, lo = the same truncation of v - hi); the product is
+// formed from hi.hi + hi.lo + lo.hi, and |x - c|^2 enters as hi + lo times 1.
+// One tcgen05.mma of kind::tf32 with K = 8 covers two coordinates' worth of
+// those columns; a node row has KT = 3d + 2 columns rounded up to a multiple of 8.
+#pragma once
+#include "pakr_internal.h"
+
+namespace pakr {
+
+// ---------------------------------------------------------------------------
+// PTX wrappers (sm_100 family).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long tc_clock_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Wait for the phase with the given parity for at most limit_ns of device
+// time; false on timeout.  Polls with the non-blocking test; after 64 failed
+// polls the thread sleeps between polls (32 ns doubling to 256 ns).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, unsigned long long limit_ns)
+{
+    if (mbar_test_wait(bar, parity))
+        return true;
+    const unsigned long long t0 = tc_clock_ns();
+    unsigned ns = 32;
+    for (int it = 0;; ++it) {
+        if (mbar_test_wait(bar, parity))
+            return true;
+        if (it >= 64) {
+            __nanosleep(ns);
+            ns = ns < 256 ? 2 * ns : 256;
+        }
+        if ((it & 15) == 15 && tc_clock_ns() - t0 > limit_ns)
+            return false;
+    }
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::tf32, one CTA.
+__device__ __forceinline__ void mma_tf32_ss(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "setp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                 "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
+// Arrive on the mbarrier when every tcgen05 operation this thread issued so far has completed.
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// Order this thread's generic-proxy shared-memory writes before later async-proxy (TMA, MMA) accesses.
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Bulk copy global -> shared (addresses 16-byte aligned, bytes a multiple of 16), completing on the
+// mbarrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst_smem, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst_smem),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// Two loads of 32 consecutive FP32 accumulator columns of this thread's TMEM lane
+// (at taddr and taddr + 32), then the wait for both.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64])
+{
+    uint32_t r[64];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+                 "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]),
+                   "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
+                   "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
+                   "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+                   "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+                 : "r"(taddr), "r"(taddr + 32u)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+// Minimum of 16 values: a depth-3 tree of three-input minima.
+__device__ __forceinline__ float min16(const float *w)
+{
+    const float a = fmin3(w[0], w[1], w[2]);
+    const float b = fmin3(w[3], w[4], w[5]);
+    const float c = fmin3(w[6], w[7], w[8]);
+    const float d = fmin3(w[9], w[10], w[11]);
+    const float e = fmin3(w[12], w[13], w[14]);
+    return fminf(fmin3(a, b, c), fmin3(d, e, w[15]));
+}
+
+// Shared-memory matrix descriptor, no swizzle, K-major: LBO = byte distance of
+// the two core matrices along K, SBO = byte distance of 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ---------------------------------------------------------------------------
+// Operand geometry.
+// ---------------------------------------------------------------------------
+constexpr int kTcM = 128;        // queries per CTA (MMA M)
+constexpr int kTcN = 256;        // nodes per tile (MMA N); two accumulators fill the 512 TMEM columns
+constexpr int kTcAcc = 2;
+constexpr int kTcReaders = 256;  // 8 accumulator-reader warps: two per TMEM lane quarter, one column half each
+constexpr int kTcG = 16;         // nodes per filter group
+constexpr int kTcRing = 8;       // candidate groups remembered per (query, reader)
+constexpr float kTcSentinel = 1.2676506e30f;  // 2^100: |x - c|^2 of ineligible and padding nodes
+constexpr float kTcEligible = 6.338253e29f;   // 2^99: filter values at or above are not eligible nodes
+// warp roles
+constexpr int kTcLoadWarp = 0;   // lane 0: bulk copies of node tiles and f-costs
+constexpr int kTcPatch0 = 1;     // warps 1-4: mask ineligible rows, signal "tile ready"
+constexpr int kTcMmaWarp = 5;    // lane 0: MMAs; the warp owns the TMEM allocation
+constexpr int kTcReader0 = 6;    // warps 6-13: accumulator readers
+constexpr int kTcThreads = kTcReader0 * 32 + kTcReaders;
+
+template <int D>
+struct TcShape {
+    static constexpr int KT = ((3 * D + 2) + 7) / 8 * 8;  // x_hi, x_lo, x_hi, |x|^2 hi, lo, zero padding
+    static constexpr int LBO = 128, SBO = KT * 32;         // no-swizzle K-major core-matrix layout
+    static constexpr int TILE_BYTES = kTcN * KT * 4;       // one packed node tile, contiguous
+    static constexpr int A_BYTES = kTcM * KT * 4;
+    static constexpr int F_BYTES = kTcN * 4;
+    static constexpr int RING_BYTES = kTcRing * kTcReaders * 8;
+    static constexpr int NSTAGE_FIT = (200 * 1024 - A_BYTES - RING_BYTES) / (TILE_BYTES + F_BYTES);
+    static constexpr int NSTAGE = NSTAGE_FIT > 6 ? 6 : NSTAGE_FIT;  // node tiles staged in shared memory
+    static constexpr int SMEM = A_BYTES + NSTAGE * (TILE_BYTES + F_BYTES) + RING_BYTES;
+    // at least enough dynamic shared memory that a CTA holds an SM alone (it allocates all 512 TMEM columns)
+    static constexpr int SMEM_REQ = SMEM > 120 * 1024 ? SMEM : 120 * 1024;
+};
+
+// Byte offset of (row r, column k) in a no-swizzle K-major tile with KT columns.
+template <int D>
+__host__ __device__ __forceinline__ uint32_t tc_off(int r, int k)
+{
+    return (uint32_t)((r >> 3) * TcShape<D>::SBO + (k >> 2) * TcShape<D>::LBO + (r & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ float tf32_trunc(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+
+// Bound on |a + |q - c|^2 - e| relative to R^2 = (|q - c| + X)^2, with e the exact FP32
+// squared distance the result is defined by and X the bound on |x - c| over the state box.
+// Terms (u = 2^-24): the hi/lo truncations leave |v - hi - lo| < 2^-20 |v| per operand, so
+// the three partial products miss -2 q.x by at most 6 2^-20 |q||x| <= 1.5 2^-20 R^2, and
+// |x|^2 by 2^-20 |x|^2; FP32 |x - c|^2 adds gamma_d; the exact form e carries gamma_(d+2);
+// rounding x - c and q - c moves the distance by at most 2.01 u R^2; the tensor-core
+// accumulation is taken as 4 (KT/8 + 1) u of the sum of |products| (measured on this GPU
+// at most 5.2 u with 5 accumulating k-steps, 2.2 u with one).  The total is doubled.
+template <int D>
+__host__ __device__ constexpr float tc_bound_coef()
+{
+    constexpr float u = 5.9604645e-8f;
+    constexpr int KT = TcShape<D>::KT;
+    return 2.f * (2.5f * 16.f * u + D * u / (1.f - D * u) + (D + 2) * u / (1.f - (D + 2) * u) +
+                  1.01f * 4.f * (KT / 8 + 1) * u + 2.01f * u);
+}
+
+// Write node j's packed operand row (state x, unweighted) into the tree's tile copy;
+// flag the tree when |x_w - c|^2 exceeds the box bound the error analysis assumes.
+template <int D>
+__device__ __forceinline__ void tc_pack_node(const DevProblem &P, const DevTree &T, Ctl *ctl, int j, const float *x)
+{
+    if (!T.XT)
+        return;
+    constexpr int KT = TcShape<D>::KT;
+    float row[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k)
+        row[k] = 0.f;
+    float xn = 0.f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const float v = x[a] * P.sw[a] - P.tc_c[a];
+        xn = __fmaf_rn(v, v, xn);
+        const float hi = tf32_trunc(v);
+        row[a] = hi;
+        row[D + a] = tf32_trunc(v - hi);
+        row[2 * D + a] = hi;
+    }
+    const float nh = tf32_trunc(xn);
+    row[3 * D] = nh;
+    row[3 * D + 1] = tf32_trunc(xn - nh);
+    if (!(xn <= P.tc_xbox2))
+        atomicOr(&ctl->tc_flag, 1u);
+    unsigned char *tile = reinterpret_cast<unsigned char *>(T.XT) + (size_t)(j / kTcN) * TcShape<D>::TILE_BYTES;
+    const int r = j % kTcN;
+#pragma unroll
+    for (int c = 0; c < KT / 4; ++c)
+        *reinterpret_cast<float4 *>(tile + tc_off<D>(r, 4 * c)) =
+            make_float4(row[4 * c], row[4 * c + 1], row[4 * c + 2], row[4 * c + 3]);
+}
+
+}  // namespace pakr

@@ -35,6 +35,9 @@ _PI64 = C.POINTER(C.c_int64)
 _PD = C.POINTER(C.c_double)
 
 
+NN_AUTO, NN_FP32, NN_TENSOR = 0, 1, 2  # pakr_nn_mode
+
+
 class ProblemDesc(C.Structure):
     _fields_ = [
         ("dynamics", C.c_int32),
@@ -48,7 +51,7 @@ class ProblemDesc(C.Structure):
         ("n_parents", C.c_int32), ("branching", C.c_int32),
         ("tree_cap", C.c_int64), ("device", C.c_int32), ("cuda_stream", C.c_void_p),
         ("workspace", C.c_void_p), ("workspace_bytes", C.c_uint64),
-        ("path_cap", C.c_int32), ("history_cap", C.c_int32),
+        ("path_cap", C.c_int32), ("history_cap", C.c_int32), ("nn_mode", C.c_int32),
     ]
 
 
@@ -215,6 +218,7 @@ def problem_desc(spec, arr):
     desc.model_params = arr(spec["model"]) if spec["dyn"] == QUAD12 else None
     desc.n_parents, desc.branching = spec["K"], spec["k"]
     desc.tree_cap = spec["cap"]
+    desc.nn_mode = int(spec.get("nn_mode", NN_AUTO))
     return desc
 
 

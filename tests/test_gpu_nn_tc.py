@@ -1,0 +1,121 @@
+"""Tensor-core nearest neighbour (k_nn_tc) against the FP32 kernel and the oracle.
+
+Both kernels define the result the same way (the exact FP32 squared distance,
+lowest index on a tie), so on the same tree, samples and bound the chosen
+parents must be identical, element by element.  Trees come from the seeded
+generators; the planners are forced to one kernel with nn_mode.
+"""
+import numpy as np
+import pytest
+
+from paper_2607_03987_gb300 import pakr
+from paper_2607_03987_gb300 import workloads as W
+from parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+def expand_near(spec, tree, bound, seed, mode):
+    planner = pakr.Planner(W.with_sizes(spec, nn_mode=mode))
+    try:
+        planner.tree_import(tree, spec["x_goal"])
+        st, info = planner.expand(bound, seed)
+        dbg = planner.debug_last_expand()
+    finally:
+        planner.close()
+    return st, info, dbg
+
+
+def assert_same_expansion(spec, tree, bound, seed):
+    s1, i1, d1 = expand_near(spec, tree, bound, seed, pakr.NN_FP32)
+    s2, i2, d2 = expand_near(spec, tree, bound, seed, pakr.NN_TENSOR)
+    assert s1 == s2
+    assert np.array_equal(d1["samples"], d2["samples"])
+    bad = np.nonzero(d1["near"] != d2["near"])[0]
+    assert bad.size == 0, f"parents differ at queries {bad[:10]}: fp32 {d1['near'][bad[:10]]} tc {d2['near'][bad[:10]]}"
+    # identical parents give identical rollouts and the same appended tree
+    assert np.array_equal(d1["outcome"], d2["outcome"])
+    assert i1 == i2
+    return d1
+
+
+@pytest.mark.parametrize("name,K,k,n", [
+    ("di3", 1024, 8, 300_000),      # several query blocks, many 256-node tiles per chunk
+    ("di3", 1000, 4, 123_457),      # ragged query block and ragged last tile
+    ("di2", 300, 3, 70_001),
+    ("quad12", 512, 4, 100_000),    # d = 12: five MMA k-steps
+])
+def test_tc_matches_fp32_uniform(cuda_lib, name, K, k, n):
+    spec = W.with_sizes(W.problem(name, env_seed=3), K=K, k=k, cap=n + 64)
+    tree = W.prefilled_tree(spec, n, seed=9)
+    d = assert_same_expansion(spec, tree, np.inf, seed=17)
+    assert (d["near"] >= 0).all()
+
+
+def test_tc_matches_fp32_finite_bound(cuda_lib):
+    # costs uniform in [0, 3]: a finite bound leaves part of the tree ineligible
+    spec = W.with_sizes(W.problem("di3", env_seed=4), K=1024, k=4, cap=200_064)
+    tree = W.prefilled_tree(spec, 200_000, seed=10, cost_hi=3.0)
+    for bound in (2.5, 1.4):
+        assert_same_expansion(spec, tree, bound, seed=31)
+
+
+def test_tc_matches_fp32_lattice_ties(cuda_lib):
+    # states on a coarse lattice: many exactly equal distances, the lowest index must win
+    spec = W.with_sizes(W.problem("di3", env_seed=5), K=512, k=2, cap=80_000)
+    tree = W.prefilled_tree(spec, 80_000, seed=12)
+    tree["states"] = W.f32(np.round(tree["states"] * 8.0) / 8.0)
+    tree["states"][0] = spec["x_init"]
+    assert_same_expansion(spec, tree, np.inf, seed=5)
+
+
+def test_tc_matches_fp32_offset_box(cuda_lib):
+    # a state box far from the origin: the filter works on centred coordinates
+    spec = W.problem("di3", env_seed=6)
+    off = np.array([50.0, 50.0, 50.0, 0, 0, 0])
+    spec = W.with_sizes(spec, K=512, k=2, cap=70_000,
+                        x_lo=W.f32(spec["x_lo"] + off), x_hi=W.f32(spec["x_hi"] + off),
+                        x_init=W.f32(spec["x_init"] + off), x_goal=W.f32(spec["x_goal"] + off),
+                        boxes=W.f32(spec["boxes"] + np.concatenate([off[:3], off[:3]])))
+    tree = W.prefilled_tree(spec, 70_000, seed=13)
+    assert_same_expansion(spec, tree, np.inf, seed=6)
+
+
+def test_tc_small_and_out_of_box_trees(cuda_lib):
+    spec = W.with_sizes(W.problem("di3", env_seed=7), K=256, k=2, cap=4096)
+    # a tree smaller than one tile
+    tree = W.prefilled_tree(spec, 77, seed=14)
+    assert_same_expansion(spec, tree, np.inf, seed=8)
+    # states outside the state box (imported, not grown): the tree is flagged and the
+    # tensor-core kernel rescans exactly
+    tree = W.prefilled_tree(spec, 3000, seed=15)
+    tree["states"][1:40, 0] = W.f32(7.5)
+    assert_same_expansion(spec, tree, np.inf, seed=9)
+
+
+def test_tc_against_oracle(cuda_lib):
+    # the oracle's parity rules (element by element, exemptions for near-ties) on the tensor-core path
+    spec = W.with_sizes(W.problem("di3", env_seed=8), K=1024, k=2, cap=104_096, nn_mode=pakr.NN_TENSOR)
+    tree = W.prefilled_tree(spec, 100_000, seed=16)
+    planner = pakr.Planner(spec)
+    try:
+        stats = compare(spec, tree, np.inf, 41, planner)
+    finally:
+        planner.close()
+    assert stats["compared_children"] > 0
+
+
+def test_tc_plan_matches_fp32(cuda_lib):
+    # a whole AO-x run crosses the size threshold and restarts: both modes give the same history
+    spec = W.with_sizes(W.problem("di3", env_seed=0), cap=300_000)
+    res = []
+    for mode in (pakr.NN_FP32, pakr.NN_AUTO):
+        planner = pakr.Planner(W.with_sizes(spec, nn_mode=mode))
+        try:
+            res.append(planner.plan(spec["x_init"], spec["x_goal"], budget_s=60.0, max_iterations=60, seed=3))
+        finally:
+            planner.close()
+    a, b = res
+    assert a["iterations"] == b["iterations"]
+    assert np.array_equal(a["history_cost"], b["history_cost"])
+    assert np.array_equal(a["history_iteration"], b["history_iteration"])
