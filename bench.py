@@ -125,15 +125,42 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_nn launch on the bench workload
-# (n = 1,000,000 nodes, d = 6), from one ncu capture of the current kernel.
-NN_DRAM_BYTES_NCU = 28.10e6
+# dram__bytes_read.sum + dram__bytes_write.sum of one tensor-core nearest-neighbour launch
+# (k_nn_tc) on the bench workload (n = 1,000,000 nodes, d = 6) from one ncu capture of the
+# current kernel; None until that capture exists.
+NN_DRAM_BYTES_NCU = None
+
+# Nominal dense TF32 / BF16 tensor throughput ratio (1.1 / 2.25 PFLOP/s): the TF32 peak is
+# the measured BF16 GEMM rate times this.
+TF32_PER_BF16 = 1.1 / 2.25
 
 
 def nn_flops_per_launch(K, n, d):
     """Algorithmic FP32 work of one nearest-neighbour pass: a subtract, a
     multiply and an add per coordinate of every (query, node) pair."""
     return 3.0 * K * n * d
+
+
+def nn_tc_flops_per_launch(K, n, d):
+    """Algorithmic tensor-core work of the filter: per (query, node) pair the three
+    TF32 partial products of d coordinates and the two |x|^2 columns, 2 flop each."""
+    return 2.0 * K * n * (3 * d + 2)
+
+
+def nn_tc_mma_flops_per_launch(K, n, d):
+    """Tensor-core work as issued: queries padded to 128-row blocks, nodes to 256-node
+    tiles, operand columns to a multiple of 8."""
+    kt = ((3 * d + 2) + 7) // 8 * 8
+    return 2.0 * (-(-K // 128) * 128) * (-(-n // 256) * 256) * kt
+
+
+def nn_uses_tensor_cores(spec, n):
+    """Whether the planner's default nearest-neighbour choice (nn_mode auto) takes the
+    tensor-core kernel for a tree of n nodes."""
+    mode = spec.get("nn_mode", 0)
+    if mode == 2:
+        return True
+    return mode == 0 and spec["K"] >= 256 and n >= 65536
 
 
 def nn_bytes_per_launch(n, d):
@@ -229,7 +256,6 @@ def tree_size_sweep(dev, stream, steps=10, warmup=3):
             for w in range(warmup):
                 planner.tree_truncate(n)
                 planner.expand(np.inf, 900 + w, info=False)
-            planner.set_profiling(True)
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
             for s_, (a, b) in enumerate(ev):
                 planner.tree_truncate(n)
@@ -239,9 +265,15 @@ def tree_size_sweep(dev, stream, steps=10, warmup=3):
                 b.record(stream)
             torch.cuda.synchronize(dev)
             ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+            planner.set_profiling(True)  # per-kernel times: a second pass with per-launch events
+            for s_ in range(steps):
+                planner.tree_truncate(n)
+                flush.zero_()
+                planner.expand(np.inf, 500 + s_, info=False)
             kt = planner.kernel_times()
             planner.set_profiling(False)
-            nn_ms = kt["k_nn"]["ms"] / max(kt["k_nn"]["launches"], 1)
+            nk = "k_nn_tc" if nn_uses_tensor_cores(spec, n) else "k_nn"
+            nn_ms = kt[nk]["ms"] / max(kt[nk]["launches"], 1)
             out.append({"workload": name, "n": n, "parents": spec["K"], "branching": spec["k"],
                         "rollouts_per_s": R / (ms * 1e-3), "ms_per_step": ms,
                         "nn_ms": nn_ms, "nn_tflops": nn_flops_per_launch(spec["K"], n, spec["d"]) / (nn_ms * 1e-3) / 1e12,
@@ -491,10 +523,10 @@ def main():
         one_step(10_000 + w)
     torch.cuda.synchronize(dev)
 
-    # ---- device-timed steps (value) ----
+    # ---- device-timed steps (value): each step is one expansion graph (sample, the nearest-
+    # neighbour kernel the tree size selects, propagate, append) plus the truncation kernel ----
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    planner.set_profiling(True)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -511,10 +543,17 @@ def main():
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     local_s = sum(step_ms) / 1e3
+    value, t_max, units = aggregate(R * args.steps, local_s)
+    launches = args.steps * 4  # sample, one nearest-neighbour kernel, propagate, append per step
+
+    # ---- per-kernel device times: a separate pass with per-launch CUDA events ----
+    planner.set_profiling(True)
+    for s in range(min(args.steps, 300)):
+        planner.tree_truncate(N_PREFILL)
+        flush.zero_()
+        one_step(20_000 + s)
     kt = planner.kernel_times()
     planner.set_profiling(False)
-    value, t_max, units = aggregate(R * args.steps, local_s)
-    launches = sum(v["launches"] for v in kt.values())
 
     if args.only_expand:
         if rank == 0:
@@ -540,22 +579,37 @@ def main():
     e2e_value, _, _ = aggregate(R * args.steps, sum(e2e_times))
 
     # ---- roofline of the dominant kernel ----
-    nn = kt["k_nn"]
+    nn = kt["k_nn_tc"] if nn_uses_tensor_cores(spec, N_PREFILL) else kt["k_nn"]
     nn_ms = nn["ms"] / max(nn["launches"], 1)
-    flops = nn_flops_per_launch(spec["K"], N_PREFILL, spec["d"])
     peaks, peak_src = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak_tflops = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
-    achieved = flops / (nn_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak_tflops, "traffic": NN_DRAM_BYTES_NCU, "kernel": "k_nn",
-                "traffic_unit": "DRAM bytes read + written per k_nn launch (ncu, this kernel and workload)",
-                "peak_source": f"FP32 FFMA: {props.multi_processor_count} SMs x 128 lanes x 2 flop x "
-                               f"{sm_mhz:.0f} MHz ({peak_src} max SM clock)",
-                "nn_ms_per_launch": nn_ms,
-                "nn_dram_gbs_algorithmic": nn_bytes_per_launch(N_PREFILL, spec["d"]) / (nn_ms * 1e-3) / 1e9,
-                "kernel_ms_per_step": {k: v["ms"] / max(v["launches"], 1) for k, v in kt.items()}}
+    fp32_equiv = nn_flops_per_launch(spec["K"], N_PREFILL, spec["d"]) / (nn_ms * 1e-3) / 1e12
+    if nn_uses_tensor_cores(spec, N_PREFILL):
+        tf32_peak = float(peaks["bf16_tflops"]) * TF32_PER_BF16
+        achieved = nn_tc_flops_per_launch(spec["K"], N_PREFILL, spec["d"]) / (nn_ms * 1e-3) / 1e12
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / tf32_peak, "traffic": NN_DRAM_BYTES_NCU, "kernel": "k_nn_tc",
+                    "traffic_unit": "DRAM bytes read + written per k_nn_tc launch (ncu, this kernel and workload)",
+                    "peak_source": f"TF32 dense = {peak_src} BF16 GEMM {float(peaks['bf16_tflops']):.0f} TFLOP/s "
+                                   f"x nominal TF32/BF16 ratio 1.1/2.25",
+                    "work": "2 K n (3d + 2): three TF32 partial products per coordinate and |x|^2 hi, lo",
+                    "mma_issued_tflops": nn_tc_mma_flops_per_launch(spec["K"], N_PREFILL, spec["d"])
+                    / (nn_ms * 1e-3) / 1e12,
+                    "fp32_equivalent_tflops": fp32_equiv,
+                    "fp32_ffma_peak_tflops": fp32_peak_tflops,
+                    "nn_ms_per_launch": nn_ms,
+                    "nn_dram_gbs_algorithmic": nn_bytes_per_launch(N_PREFILL, spec["d"]) / (nn_ms * 1e-3) / 1e9,
+                    "kernel_ms_per_step": {k: v["ms"] / max(v["launches"], 1) for k, v in kt.items()}}
+    else:
+        roofline = {"bound": "alu", "achieved": fp32_equiv, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                    "frac": fp32_equiv / fp32_peak_tflops, "traffic": None, "kernel": "k_nn",
+                    "peak_source": f"FP32 FFMA: {props.multi_processor_count} SMs x 128 lanes x 2 flop x "
+                                   f"{sm_mhz:.0f} MHz ({peak_src} max SM clock)",
+                    "nn_ms_per_launch": nn_ms,
+                    "nn_dram_gbs_algorithmic": nn_bytes_per_launch(N_PREFILL, spec["d"]) / (nn_ms * 1e-3) / 1e9,
+                    "kernel_ms_per_step": {k: v["ms"] / max(v["launches"], 1) for k, v in kt.items()}}
 
     # ---- planning metrics: p50 time to first solution, AO-x cost at 100 ms ----
     plan_spec = W.problem(WORKLOAD, env_seed=0)

@@ -283,7 +283,10 @@ pakr_status pakr_debug_last_expand(pakr_planner *planner, float *samples, int32_
  * milliseconds, measured with CUDA events on the planner's stream around each
  * launch.  pakr_set_profiling(p, 1) clears and starts, 0 stops.  names_out
  * (optional) receives a static string per slot.  Slots: 0 sample, 1 nearest
- * neighbour, 2 propagate, 3 append.  launches_out counts launches per slot. */
+ * neighbour (FP32 kernel), 2 propagate, 3 append, 4 nearest neighbour (tensor-core
+ * kernel).  launches_out counts launches per slot.  While profiling, pakr_expand
+ * launches its kernels one by one (both nearest-neighbour kernels, the one not
+ * taken returning at once); otherwise it launches one CUDA graph per expansion. */
 pakr_status pakr_set_profiling(pakr_planner *planner, int32_t enable);
 pakr_status pakr_kernel_times(pakr_planner *planner, double *ms_out, int64_t *launches_out, const char **names_out,
                               int32_t n_slots);

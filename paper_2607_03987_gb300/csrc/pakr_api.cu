@@ -219,6 +219,9 @@ struct EventPair {
     cudaEvent_t a, b;
 };
 
+// Per-kernel timing slots of pakr_kernel_times.
+constexpr int kTimeSlots = 5;
+
 }  // namespace
 
 struct pakr_planner {
@@ -243,12 +246,17 @@ struct pakr_planner {
     int path_cap = 0, hist_cap = 0;
     cudaGraphExec_t plan_exec = nullptr;
     cudaGraph_t plan_graph = nullptr;
+    // one expansion as a graph (pakr_expand without profiling): its sample node takes
+    // the bound and seed of each call
+    cudaGraphExec_t expand_exec = nullptr;
+    cudaGraph_t expand_graph = nullptr;
+    cudaGraphNode_t expand_sample = nullptr;
     // profiling
     bool profiling = false;
     std::vector<EventPair> pool;
     std::vector<std::pair<int, EventPair>> pending;
-    double ms[4] = {0, 0, 0, 0};
-    int64_t launches[4] = {0, 0, 0, 0};
+    double ms[kTimeSlots] = {0, 0, 0, 0, 0};
+    int64_t launches[kTimeSlots] = {0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -307,15 +315,141 @@ pakr_status enqueue_expand(pakr_planner *p, float bound, uint64_t seed)
                "sample");
     if (st != PAKR_OK)
         return st;
-    st = timed(p, 1, [&] { return launch_nn(p->P, p->ctl, p->T, p->W, p->L, p->stream); }, "nearest");
-    if (st != PAKR_OK)
-        return st;
+    // both nearest-neighbour kernels; each returns at once unless the tree size is its range
+    if (p->P.tc_min_n > 0) {
+        st = timed(p, 1, [&] { return launch_nn_fp32(p->P, p->ctl, p->T, p->W, p->L, p->stream); }, "nearest");
+        if (st != PAKR_OK)
+            return st;
+    }
+    if (p->T.XT && p->P.tc_min_n < 0x7FFFFFFF) {
+        st = timed(p, 4, [&] { return launch_nn_tc(p->P, p->ctl, p->T, p->W, p->L, p->stream); }, "nearest (tc)");
+        if (st != PAKR_OK)
+            return st;
+    }
     st = timed(p, 2, [&] { return launch_propagate(p->P, p->ctl, p->T, p->W, p->L, p->stream); }, "propagate");
     if (st != PAKR_OK)
         return st;
     return timed(p, 3, [&] { return launch_append(p->P, p->ctl, p->T, p->W, p->L, p->stream); }, "append");
 }
 
+// The nodes of g that are not in `before`.
+std::vector<cudaGraphNode_t> new_nodes(cudaGraph_t g, const std::vector<cudaGraphNode_t> &before)
+{
+    size_t n = 0;
+    cudaGraphGetNodes(g, nullptr, &n);
+    std::vector<cudaGraphNode_t> all(n), out;
+    if (n)
+        cudaGraphGetNodes(g, all.data(), &n);
+    for (cudaGraphNode_t x : all)
+        if (std::find(before.begin(), before.end(), x) == before.end())
+            out.push_back(x);
+    return out;
+}
+
+std::vector<cudaGraphNode_t> graph_nodes(cudaGraph_t g)
+{
+    return new_nodes(g, {});
+}
+
+// Capture `launch` into graph g after the node `dep` (none if nullptr); returns the
+// single node it adds in *node.
+template <class F>
+pakr_status capture_one(pakr_planner *p, cudaGraph_t g, cudaGraphNode_t dep, F &&launch, cudaGraphNode_t *node)
+{
+    const std::vector<cudaGraphNode_t> before = graph_nodes(g);
+    CUDA_TRY(cudaStreamBeginCaptureToGraph(p->capture_stream, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0,
+                                           cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = launch(p->capture_stream);
+    cudaGraph_t tmp = nullptr;
+    CUDA_TRY(cudaStreamEndCapture(p->capture_stream, &tmp));
+    CUDA_TRY(le);
+    const std::vector<cudaGraphNode_t> added = new_nodes(g, before);
+    if (added.size() != 1)
+        return fail(PAKR_ERR_CUDA, "unexpected graph shape (%zu nodes captured)", added.size());
+    *node = added[0];
+    return PAKR_OK;
+}
+
+// An IF node on handle h after `dep`, whose body holds the one launch `launch`.
+template <class F>
+pakr_status add_if(pakr_planner *p, cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle h, F &&launch,
+                   cudaGraphNode_t *node)
+{
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    CUDA_TRY(cudaGraphAddNode(node, g, &dep, nullptr, 1, &cp));
+    cudaGraphNode_t inner = nullptr;
+    return capture_one(p, cp.conditional.phGraph_out[0], nullptr, launch, &inner);
+}
+
+// Which nearest-neighbour kernel an expansion graph runs.
+enum NnKind { NN_SELECT = 0, NN_ONLY_FP32 = 1, NN_ONLY_TC = 2 };
+
+// Append one expansion to graph g after `dep`: sample, nearest neighbour, propagate,
+// append.  NN_SELECT with the packed tree copy puts k_nn and k_nn_tc in IF nodes that
+// k_sample opens one of; otherwise the one kernel runs as a plain node.
+pakr_status add_expansion(pakr_planner *p, cudaGraph_t g, cudaGraphNode_t dep, float bound, uint64_t seed, int mode,
+                          NnKind kind, cudaGraphNode_t *sample_node, cudaGraphNode_t *last)
+{
+    const bool cond = kind == NN_SELECT && p->T.XT != nullptr;
+    cudaGraphConditionalHandle h[2]{};
+    if (cond) {
+        CUDA_TRY(cudaGraphConditionalHandleCreate(&h[0], g, 0, cudaGraphCondAssignDefault));
+        CUDA_TRY(cudaGraphConditionalHandleCreate(&h[1], g, 0, cudaGraphCondAssignDefault));
+    }
+    pakr_status st = capture_one(
+        p, g, dep,
+        [&](cudaStream_t s) { return launch_sample(p->P, p->ctl, p->W, p->L, bound, seed, mode, s, cond ? h : nullptr); },
+        sample_node);
+    if (st != PAKR_OK)
+        return st;
+    cudaGraphNode_t at = *sample_node;
+    if (cond) {
+        st = add_if(p, g, at, h[0],
+                    [&](cudaStream_t s) { return launch_nn_fp32(p->P, p->ctl, p->T, p->W, p->L, s); }, &at);
+        if (st != PAKR_OK)
+            return st;
+        st = add_if(p, g, at, h[1],
+                    [&](cudaStream_t s) { return launch_nn_tc(p->P, p->ctl, p->T, p->W, p->L, s); }, &at);
+    } else if (kind == NN_ONLY_TC) {
+        st = capture_one(p, g, at, [&](cudaStream_t s) { return launch_nn_tc(p->P, p->ctl, p->T, p->W, p->L, s); },
+                         &at);
+    } else {
+        st = capture_one(p, g, at, [&](cudaStream_t s) { return launch_nn_fp32(p->P, p->ctl, p->T, p->W, p->L, s); },
+                         &at);
+    }
+    if (st != PAKR_OK)
+        return st;
+    st = capture_one(p, g, at, [&](cudaStream_t s) { return launch_propagate(p->P, p->ctl, p->T, p->W, p->L, s); },
+                     &at);
+    if (st != PAKR_OK)
+        return st;
+    st = capture_one(p, g, at, [&](cudaStream_t s) { return launch_append(p->P, p->ctl, p->T, p->W, p->L, s); }, &at);
+    *last = at;
+    return st;
+}
+
+// Add a WHILE node on handle h after `dep` (none if nullptr); *body receives its body graph.
+pakr_status add_while(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle h, cudaGraphNode_t *node,
+                      cudaGraph_t *body)
+{
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    CUDA_TRY(cudaGraphAddNode(node, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0, &cp));
+    *body = cp.conditional.phGraph_out[0];
+    return PAKR_OK;
+}
+
+// The AO-x graph: k_plan_init, then a WHILE loop of expansions, each followed by
+// k_plan_step.  With both nearest-neighbour kernels in play the loop body holds two inner
+// WHILE loops, FP32 while the tree is below tc_min_n nodes and tensor-core from there;
+// k_plan_step opens the one the next iteration needs (no IF node per iteration).
 pakr_status build_plan_graph(pakr_planner *p)
 {
     if (p->plan_exec)
@@ -324,43 +458,100 @@ pakr_status build_plan_graph(pakr_planner *p)
     CUDA_TRY(cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle h{};
     CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
-    CUDA_TRY(cudaStreamBeginCaptureToGraph(p->capture_stream, g, nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal));
-    cudaError_t le = launch_plan_init(p->P, p->ctl, p->T, p->pp, h, p->capture_stream);
-    cudaGraph_t tmp = nullptr;
-    CUDA_TRY(cudaStreamEndCapture(p->capture_stream, &tmp));
-    CUDA_TRY(le);
-    size_t n_nodes = 0;
-    CUDA_TRY(cudaGraphGetNodes(g, nullptr, &n_nodes));
-    if (n_nodes != 1)
-        return fail(PAKR_ERR_CUDA, "unexpected plan graph shape (%zu nodes)", n_nodes);
-    cudaGraphNode_t init_node;
-    CUDA_TRY(cudaGraphGetNodes(g, &init_node, &n_nodes));
-    cudaGraphNodeParams cp{};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t wnode;
-    CUDA_TRY(cudaGraphAddNode(&wnode, g, &init_node, nullptr, 1, &cp));
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    CUDA_TRY(cudaStreamBeginCaptureToGraph(p->capture_stream, body, nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal));
-    cudaError_t e1 = launch_sample(p->P, p->ctl, p->W, p->L, 0.f, 0ull, MODE_PLAN, p->capture_stream);
-    cudaError_t e2 = launch_nn(p->P, p->ctl, p->T, p->W, p->L, p->capture_stream);
-    cudaError_t e3 = launch_propagate(p->P, p->ctl, p->T, p->W, p->L, p->capture_stream);
-    cudaError_t e4 = launch_append(p->P, p->ctl, p->T, p->W, p->L, p->capture_stream);
-    cudaError_t e5 = launch_plan_step(p->P, p->ctl, p->T, p->pp, p->B, h, p->capture_stream);
-    CUDA_TRY(cudaStreamEndCapture(p->capture_stream, &tmp));
-    CUDA_TRY(e1);
-    CUDA_TRY(e2);
-    CUDA_TRY(e3);
-    CUDA_TRY(e4);
-    CUDA_TRY(e5);
+    cudaGraphNode_t init_node = nullptr;
+    pakr_status st = capture_one(
+        p, g, nullptr, [&](cudaStream_t s) { return launch_plan_init(p->P, p->ctl, p->T, p->pp, h, s); }, &init_node);
+    if (st != PAKR_OK)
+        return st;
+    cudaGraphNode_t wnode = nullptr;
+    cudaGraph_t body = nullptr;
+    st = add_while(g, init_node, h, &wnode, &body);
+    if (st != PAKR_OK)
+        return st;
+    const bool has_tc = p->T.XT != nullptr && p->P.tc_min_n < 0x7FFFFFFF;
+    const bool nested = has_tc && p->P.tc_min_n > 1;
+    cudaGraphNode_t sample_node = nullptr, last = nullptr, step = nullptr;
+    if (!nested) {
+        st = add_expansion(p, body, nullptr, 0.f, 0ull, MODE_PLAN, has_tc ? NN_ONLY_TC : NN_ONLY_FP32, &sample_node,
+                           &last);
+        if (st != PAKR_OK)
+            return st;
+        st = capture_one(
+            p, body, last, [&](cudaStream_t s) { return launch_plan_step(p->P, p->ctl, p->T, p->pp, p->B, h, s); },
+            &step);
+    } else {
+        // every run starts (and restarts) from a one-node tree: the FP32 loop first
+        cudaGraphConditionalHandle inner[2]{};
+        CUDA_TRY(cudaGraphConditionalHandleCreate(&inner[0], body, 1, cudaGraphCondAssignDefault));
+        CUDA_TRY(cudaGraphConditionalHandleCreate(&inner[1], body, 0, cudaGraphCondAssignDefault));
+        cudaGraphNode_t wa = nullptr, wb = nullptr;
+        cudaGraph_t body_a = nullptr, body_b = nullptr;
+        st = add_while(body, nullptr, inner[0], &wa, &body_a);
+        if (st == PAKR_OK)
+            st = add_while(body, wa, inner[1], &wb, &body_b);
+        for (int k = 0; k < 2 && st == PAKR_OK; ++k) {
+            cudaGraph_t bg = k == 0 ? body_a : body_b;
+            st = add_expansion(p, bg, nullptr, 0.f, 0ull, MODE_PLAN, k == 0 ? NN_ONLY_FP32 : NN_ONLY_TC,
+                               &sample_node, &last);
+            if (st == PAKR_OK)
+                st = capture_one(
+                    p, bg, last,
+                    [&](cudaStream_t s) { return launch_plan_step(p->P, p->ctl, p->T, p->pp, p->B, h, s, inner); },
+                    &step);
+        }
+        // the outer loop's condition is set at its own level, after both inner loops
+        cudaGraphNode_t cont = nullptr;
+        if (st == PAKR_OK)
+            st = capture_one(p, body, wb, [&](cudaStream_t s) { return launch_plan_cont(p->ctl, h, s); }, &cont);
+    }
+    if (st != PAKR_OK)
+        return st;
     cudaGraphExec_t exec = nullptr;
     CUDA_TRY(cudaGraphInstantiate(&exec, g, 0));
     p->plan_graph = g;
     p->plan_exec = exec;
+    return PAKR_OK;
+}
+
+pakr_status build_expand_graph(pakr_planner *p)
+{
+    if (p->expand_exec)
+        return PAKR_OK;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphNode_t sample_node = nullptr, last = nullptr;
+    pakr_status st = add_expansion(p, g, nullptr, 0.f, 0ull, MODE_EXPAND, NN_SELECT, &sample_node, &last);
+    if (st != PAKR_OK) {
+        cudaGraphDestroy(g);
+        return st;
+    }
+    cudaGraphExec_t exec = nullptr;
+    CUDA_TRY(cudaGraphInstantiate(&exec, g, 0));
+    p->expand_graph = g;
+    p->expand_exec = exec;
+    p->expand_sample = sample_node;
+    return PAKR_OK;
+}
+
+// One expansion through the graph: the sample node's bound and seed arguments are
+// replaced (a host-side update of the instantiated graph), then one graph launch.
+pakr_status launch_expand_graph(pakr_planner *p, float bound, uint64_t seed)
+{
+    pakr_status st = build_expand_graph(p);
+    if (st != PAKR_OK)
+        return st;
+    cudaKernelNodeParams kp{};
+    CUDA_TRY(cudaGraphKernelNodeGetParams(p->expand_sample, &kp));
+    void *args[16];
+    unsigned long long seed_arg = seed;
+    for (int i = 0; i < 9; ++i)
+        args[i] = kp.kernelParams[i];
+    args[kSampleArgBound] = &bound;
+    args[kSampleArgSeed] = &seed_arg;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    CUDA_TRY(cudaGraphExecKernelNodeSetParams(p->expand_exec, p->expand_sample, &kp));
+    CUDA_TRY(cudaGraphLaunch(p->expand_exec, p->stream));
     return PAKR_OK;
 }
 
@@ -659,6 +850,10 @@ void pakr_destroy(pakr_planner *p)
         cudaGraphExecDestroy(p->plan_exec);
     if (p->plan_graph)
         cudaGraphDestroy(p->plan_graph);
+    if (p->expand_exec)
+        cudaGraphExecDestroy(p->expand_exec);
+    if (p->expand_graph)
+        cudaGraphDestroy(p->expand_graph);
     for (auto &pe : p->pending)
         p->pool.push_back(pe.second);
     for (auto &ev : p->pool) {
@@ -706,7 +901,8 @@ pakr_status pakr_expand(pakr_planner *p, float cost_bound, uint64_t seed, pakr_e
     if (std::isnan(cost_bound))
         return fail(PAKR_ERR_INVALID_ARG, "cost_bound is NaN");
     DeviceGuard guard(p->device);
-    pakr_status st = enqueue_expand(p, cost_bound, seed);
+    // per-kernel timing needs events between the launches: plain launches then
+    pakr_status st = p->profiling ? enqueue_expand(p, cost_bound, seed) : launch_expand_graph(p, cost_bound, seed);
     if (st != PAKR_OK || !info)
         return st;
     st = read_ctl(p);
@@ -995,7 +1191,7 @@ pakr_status pakr_set_profiling(pakr_planner *p, int32_t enable)
     for (auto &pe : p->pending)
         p->pool.push_back(pe.second);
     p->pending.clear();
-    for (int s = 0; s < 4; ++s) {
+    for (int s = 0; s < kTimeSlots; ++s) {
         p->ms[s] = 0;
         p->launches[s] = 0;
     }
@@ -1006,7 +1202,7 @@ pakr_status pakr_set_profiling(pakr_planner *p, int32_t enable)
 pakr_status pakr_kernel_times(pakr_planner *p, double *ms_out, int64_t *launches_out, const char **names_out,
                               int32_t n_slots)
 {
-    static const char *names[4] = {"k_sample", "k_nn", "k_propagate", "k_append"};
+    static const char *names[kTimeSlots] = {"k_sample", "k_nn", "k_propagate", "k_append", "k_nn_tc"};
     if (!p || n_slots < 0)
         return fail(PAKR_ERR_INVALID_ARG, "bad argument");
     DeviceGuard guard(p->device);
@@ -1019,7 +1215,7 @@ pakr_status pakr_kernel_times(pakr_planner *p, double *ms_out, int64_t *launches
         p->pool.push_back(pe.second);
     }
     p->pending.clear();
-    for (int s = 0; s < n_slots && s < 4; ++s) {
+    for (int s = 0; s < n_slots && s < kTimeSlots; ++s) {
         if (ms_out)
             ms_out[s] = p->ms[s];
         if (launches_out)

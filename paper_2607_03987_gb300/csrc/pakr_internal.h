@@ -130,10 +130,18 @@ struct LaunchCfg {
 };
 
 // Kernel launchers (pakr_kernels.cu).  Each returns the launch error.
+// nn_cond: the two IF-node handles of a graph that holds k_nn and k_nn_tc behind
+// conditionals (k_sample opens one per batch), or nullptr for plain launches.
 cudaError_t launch_sample(const DevProblem &P, Ctl *ctl, const DevWork &W, const LaunchCfg &L, float bound,
-                          unsigned long long seed, int mode, cudaStream_t s);
+                          unsigned long long seed, int mode, cudaStream_t s,
+                          const cudaGraphConditionalHandle *nn_cond = nullptr);
+// Index of the bound and seed arguments of k_sample (for updating them in a graph).
+constexpr int kSampleArgBound = 3, kSampleArgSeed = 4;
 cudaError_t launch_nn(const DevProblem &P, const Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
                       cudaStream_t s);
+// k_nn alone (it still returns at once for trees of P.tc_min_n nodes or more).
+cudaError_t launch_nn_fp32(const DevProblem &P, const Ctl *ctl, const DevTree &T, const DevWork &W,
+                           const LaunchCfg &L, cudaStream_t s);
 cudaError_t launch_nn_tc(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
                          cudaStream_t s);
 cudaError_t launch_tc_pack(const DevProblem &P, Ctl *ctl, const DevTree &T, int count, cudaStream_t s);
@@ -148,8 +156,11 @@ cudaError_t launch_tree_reset(const DevProblem &P, Ctl *ctl, const DevTree &T, c
 cudaError_t launch_import_fcost(const DevProblem &P, Ctl *ctl, const DevTree &T, int count, cudaStream_t s);
 cudaError_t launch_plan_init(const DevProblem &P, Ctl *ctl, const DevTree &T, const PlanParams *pp,
                              cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_plan_cont(const Ctl *ctl, cudaGraphConditionalHandle h, cudaStream_t s);
+// inner: the handles of the FP32 and tensor-core inner loops of a nested AO-x graph, or nullptr.
 cudaError_t launch_plan_step(const DevProblem &P, Ctl *ctl, const DevTree &T, const PlanParams *pp,
-                             const DevPlanBufs &B, cudaGraphConditionalHandle h, cudaStream_t s);
+                             const DevPlanBufs &B, cudaGraphConditionalHandle h, cudaStream_t s,
+                             const cudaGraphConditionalHandle *inner = nullptr);
 cudaError_t launch_truncate(Ctl *ctl, int count, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int64_t n, cudaStream_t s);
 

@@ -21,8 +21,12 @@ namespace pakr {
 // ---------------------------------------------------------------------------
 // Expansion kernels.
 // ---------------------------------------------------------------------------
+// In a graph whose nearest-neighbour kernels sit in IF nodes (set_cond != 0), thread 0
+// also opens exactly one of them for this batch's tree size: h_fp32 for k_nn below
+// P.tc_min_n nodes, h_tc for k_nn_tc from there.
 template <int D>
-__global__ void k_sample(DevProblem P, Ctl *ctl, DevWork W, float bound, unsigned long long seed_arg, int mode)
+__global__ void k_sample(DevProblem P, Ctl *ctl, DevWork W, float bound, unsigned long long seed_arg, int mode,
+                         cudaGraphConditionalHandle h_fp32, cudaGraphConditionalHandle h_tc, int set_cond)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long seed = (mode == MODE_EXPAND) ? seed_arg : ctl->seed;
@@ -32,6 +36,11 @@ __global__ void k_sample(DevProblem P, Ctl *ctl, DevWork W, float bound, unsigne
         if (mode == MODE_EXPAND)
             ctl->seed = seed_arg;
         begin_batch(ctl, (mode == MODE_EXPAND) ? bound : ctl->c_best);
+        if (set_cond) {
+            const bool tc = ctl->n_start >= P.tc_min_n;
+            cudaGraphSetConditional(h_fp32, tc ? 0u : 1u);
+            cudaGraphSetConditional(h_tc, tc ? 1u : 0u);
+        }
     }
 }
 
@@ -129,16 +138,37 @@ __global__ void k_plan_init(DevProblem P, Ctl *ctl, DevTree T, const PlanParams 
 // End of one AO-x loop pass: record a solution (c_best, history, path) and
 // restart from the root, restart a full tree, stop on budget / iterations /
 // no eligible node.  One warp: lane 0 chases parents, the warp gathers rows.
+// Without nested loops h is the AO-x loop.  With them (nested != 0) h_fp32 and h_tc
+// are two inner loops, for iterations whose tree is below P.tc_min_n nodes (FP32
+// nearest neighbour) and for the rest: unless the run stops exactly one is opened,
+// chosen by the tree size the next iteration will see; stopping closes both, and
+// k_plan_cont then closes the AO-x loop.
 template <int D, int M>
 __global__ void k_plan_step(DevProblem P, Ctl *ctl, DevTree T, const PlanParams *pp, DevPlanBufs B,
-                            cudaGraphConditionalHandle h)
+                            cudaGraphConditionalHandle h, cudaGraphConditionalHandle h_fp32,
+                            cudaGraphConditionalHandle h_tc, int nested)
 {
     __shared__ int s_len;
     __shared__ int s_found;
     const bool stop = aox_step_warp<D, M>(P, ctl, T, B, pp->stop_at_first, pp->budget_ns, pp->max_iterations, &s_len,
                                           &s_found);
-    if (threadIdx.x == 0)
-        cudaGraphSetConditional(h, stop ? 0u : 1u);
+    if (threadIdx.x == 0) {
+        if (nested) {
+            const bool next_tc = ctl->count >= P.tc_min_n;
+            cudaGraphSetConditional(h_fp32, (!stop && !next_tc) ? 1u : 0u);
+            cudaGraphSetConditional(h_tc, (!stop && next_tc) ? 1u : 0u);
+        } else {
+            cudaGraphSetConditional(h, stop ? 0u : 1u);
+        }
+    }
+}
+
+// End of one pass of the outer AO-x loop of a nested graph: continue unless the last
+// k_plan_step stopped the run.
+__global__ void k_plan_cont(const Ctl *ctl, cudaGraphConditionalHandle h)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0)
+        cudaGraphSetConditional(h, ctl->plan_stop ? 0u : 1u);
 }
 
 __global__ void k_truncate(Ctl *ctl, int count)
@@ -165,10 +195,12 @@ constexpr int kNnTile = 256;
 constexpr int kNnGroup = 8;
 
 cudaError_t launch_sample(const DevProblem &P, Ctl *ctl, const DevWork &W, const LaunchCfg &L, float bound,
-                          unsigned long long seed, int mode, cudaStream_t s)
+                          unsigned long long seed, int mode, cudaStream_t s, const cudaGraphConditionalHandle *nn_cond)
 {
+    const cudaGraphConditionalHandle h0 = nn_cond ? nn_cond[0] : cudaGraphConditionalHandle{};
+    const cudaGraphConditionalHandle h1 = nn_cond ? nn_cond[1] : cudaGraphConditionalHandle{};
     PAKR_DISPATCH_DYN(P.dyn, (k_sample<Dims<DYN_>::D><<<L.sample_blocks, L.sample_threads, 0, s>>>(
-                                 P, ctl, W, bound, seed, mode)));
+                                 P, ctl, W, bound, seed, mode, h0, h1, nn_cond ? 1 : 0)));
     return cudaGetLastError();
 }
 
@@ -188,6 +220,13 @@ static cudaError_t launch_nn_d(const DevProblem &P, const Ctl *ctl, const DevTre
 // Both nearest-neighbour kernels are launched when the tree keeps the packed
 // operand copy; each returns at once unless the device-side tree size is in its
 // range (k_nn below P.tc_min_n, k_nn_tc from it), so no host read is needed.
+cudaError_t launch_nn_fp32(const DevProblem &P, const Ctl *ctl, const DevTree &T, const DevWork &W,
+                           const LaunchCfg &L, cudaStream_t s)
+{
+    PAKR_DISPATCH_DYN(P.dyn, return launch_nn_d<Dims<DYN_>::D>(P, ctl, T, W, L, s));
+    return cudaSuccess;
+}
+
 cudaError_t launch_nn(const DevProblem &P, const Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
                       cudaStream_t s)
 {
@@ -254,9 +293,19 @@ cudaError_t launch_plan_init(const DevProblem &P, Ctl *ctl, const DevTree &T, co
 }
 
 cudaError_t launch_plan_step(const DevProblem &P, Ctl *ctl, const DevTree &T, const PlanParams *pp,
-                             const DevPlanBufs &B, cudaGraphConditionalHandle h, cudaStream_t s)
+                             const DevPlanBufs &B, cudaGraphConditionalHandle h, cudaStream_t s,
+                             const cudaGraphConditionalHandle *inner)
 {
-    PAKR_DISPATCH_DYN(P.dyn, (k_plan_step<Dims<DYN_>::D, Dims<DYN_>::M><<<1, 32, 0, s>>>(P, ctl, T, pp, B, h)));
+    const cudaGraphConditionalHandle h0 = inner ? inner[0] : cudaGraphConditionalHandle{};
+    const cudaGraphConditionalHandle h1 = inner ? inner[1] : cudaGraphConditionalHandle{};
+    PAKR_DISPATCH_DYN(P.dyn, (k_plan_step<Dims<DYN_>::D, Dims<DYN_>::M><<<1, 32, 0, s>>>(P, ctl, T, pp, B, h, h0, h1,
+                                                                                           inner ? 1 : 0)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan_cont(const Ctl *ctl, cudaGraphConditionalHandle h, cudaStream_t s)
+{
+    k_plan_cont<<<1, 32, 0, s>>>(ctl, h);
     return cudaGetLastError();
 }
 

@@ -389,11 +389,11 @@ class Planner:
         return _check(lib().pakr_set_profiling(self.h, int(bool(enable))), "pakr_set_profiling")
 
     def kernel_times(self):
-        ms = (C.c_double * 4)()
-        n = (C.c_int64 * 4)()
-        names = (C.c_char_p * 4)()
-        _check(lib().pakr_kernel_times(self.h, ms, n, names, 4), "pakr_kernel_times")
-        return {names[i].decode(): dict(ms=ms[i], launches=int(n[i])) for i in range(4)}
+        ms = (C.c_double * 5)()
+        n = (C.c_int64 * 5)()
+        names = (C.c_char_p * 5)()
+        _check(lib().pakr_kernel_times(self.h, ms, n, names, 5), "pakr_kernel_times")
+        return {names[i].decode(): dict(ms=ms[i], launches=int(n[i])) for i in range(5)}
 
     def philox(self, ctr, key):
         ctr = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
