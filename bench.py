@@ -127,8 +127,9 @@ def measured_peaks():
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one tensor-core nearest-neighbour launch
 # (k_nn_tc) on the bench workload (n = 1,000,000 nodes, d = 6) from one ncu capture of the
-# current kernel; None until that capture exists.
-NN_DRAM_BYTES_NCU = None
+# current kernel (read 127.03 MB: the 96 MB packed operand copy, f-costs and the exact
+# resolve's coordinate rows; written 3.78 MB).
+NN_DRAM_BYTES_NCU = 127.03e6 + 3.78e6
 
 # Nominal dense TF32 / BF16 tensor throughput ratio (1.1 / 2.25 PFLOP/s): the TF32 peak is
 # the measured BF16 GEMM rate times this.
@@ -485,6 +486,9 @@ def main():
     ap.add_argument("--table4", action="store_true",
                     help="add the batch size x branching factor sweep on the 12D quadrotor (Table 4)")
     ap.add_argument("--table4-trials", type=int, default=20)
+    ap.add_argument("--plain-launches", action="store_true",
+                    help="launch each kernel of the timed steps separately (per-kernel profilers cannot see "
+                         "kernels inside the expansion graph's conditional nodes)")
     ap.add_argument("--only-expand", action="store_true",
                     help="time the expansion steps only (no e2e, planning metrics or CPU baseline)")
     args = ap.parse_args()
@@ -527,6 +531,8 @@ def main():
     # neighbour kernel the tree size selects, propagate, append) plus the truncation kernel ----
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if args.plain_launches:
+        planner.set_profiling(True)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -547,6 +553,7 @@ def main():
     launches = args.steps * 4  # sample, one nearest-neighbour kernel, propagate, append per step
 
     # ---- per-kernel device times: a separate pass with per-launch CUDA events ----
+    planner.set_profiling(False)
     planner.set_profiling(True)
     for s in range(min(args.steps, 300)):
         planner.tree_truncate(N_PREFILL)
