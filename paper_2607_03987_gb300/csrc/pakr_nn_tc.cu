@@ -205,15 +205,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_tf32(kTcM, kTcN);
             const uint32_t a_addr = smem_u32(sA), b_addr = smem_u32(sB0);
-            for (int t = 0; t < ntiles && !s_abort; ++t) {
+            // no per-tile poll of the abort flag (a shared-memory load that queues behind the
+            // tile traffic): the masking warps signal every tile even after an abort, and a
+            // wait that times out ends the loop
+            for (int t = 0; t < ntiles; ++t) {
                 const int st = t % NST, ac = t % kTcAcc;
                 if (!mbar_wait_bounded(smem_u32(&s_full[st]), (t / NST) & 1, kWaitNs)) {
                     s_abort = 1;
                     atomicOr(&ctl->err, ERR_TC_TIMEOUT);
                     break;
                 }
-                if (s_abort)
-                    break;
                 tc_fence_after();
 #pragma unroll
                 for (int s = 0; s < KT / 8; ++s)
@@ -237,8 +238,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         band = 2.f * tc_bound_coef<D>() * Rq * Rq;
         float thr = kTcEligible;
         for (int t = 0; t < ntiles; ++t) {
-            if (__any_sync(0xFFFFFFFFu, s_abort != 0))
-                break;
             const int b = t % kTcAcc;
             const bool ok =
                 __all_sync(0xFFFFFFFFu, mbar_wait_bounded(smem_u32(&s_done[b]), (t / kTcAcc) & 1, kWaitNs));
