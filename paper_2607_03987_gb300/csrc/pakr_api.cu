@@ -607,6 +607,8 @@ pakr_status pakr::fill_problem(const pakr_problem_desc *desc, DevProblem *P, int
     P->heuristic = d.heuristic;
     P->K = d.n_parents;
     P->k = d.branching;
+    for (int a = 0; a < kMaxD; ++a)  // nearest-neighbour coordinates are centred on the state box
+        P->tc_c[a] = a < di.d ? 0.5f * (d.x_lo[a] + d.x_hi[a]) * P->sw[a] : 0.f;
     *d_out = di.d;
     *m_out = di.m;
     *pdim_out = di.pdim;

@@ -317,7 +317,10 @@ __device__ __forceinline__ void begin_batch(Ctl *ctl, float bound)
 //
 // Result: for each query the eligible node (f-cost below the bound) with the
 // smallest exact FP32 squared distance  e = sum_a fl(q_a - x_a)^2  (FADD then
-// FMA per coordinate, in coordinate order), the lowest index on a tie.
+// FMA per coordinate, in coordinate order), the lowest index on a tie.  The
+// coordinates are the weighted states centred on the state box:
+// q_a = fl(fl(q_a sw_a) - c_a), the same values the tensor-core kernel keeps
+// in its packed copy (P.tc_c = c; zero where no box is known).
 //
 // Scan: block (chunk c, query group g) holds 2*QP queries per thread as QP
 // float2 pairs and streams its node range in TILE-node tiles through shared
@@ -358,7 +361,7 @@ __device__ __forceinline__ float exact_dist2(const DevProblem &P, const DevTree 
     float acc = 0.f;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        const float nx = -(T.X[(size_t)a * P.cap + j] * P.sw[a]);
+        const float nx = -__fsub_rn(__fmul_rn(T.X[(size_t)a * P.cap + j], P.sw[a]), P.tc_c[a]);
         const float diff = __fadd_rn(qv[a], nx);
         acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
     }
@@ -419,7 +422,7 @@ __device__ __forceinline__ void nn_scan(const DevProblem &P, const DevTree &T, c
         float s = 0.f;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            qs[qi][a] = (qid < K) ? W.xr[(size_t)a * K + qid] * P.sw[a] : 0.f;
+            qs[qi][a] = (qid < K) ? __fsub_rn(__fmul_rn(W.xr[(size_t)a * K + qid], P.sw[a]), P.tc_c[a]) : 0.f;
             s = __fmaf_rn(qs[qi][a], qs[qi][a], s);
         }
         qn[qi] = s;
@@ -450,7 +453,7 @@ __device__ __forceinline__ void nn_scan(const DevProblem &P, const DevTree &T, c
             float xn = 0.f;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                const float v = in ? T.X[(size_t)a * cap + j] * P.sw[a] : 0.f;
+                const float v = in ? __fsub_rn(__fmul_rn(T.X[(size_t)a * cap + j], P.sw[a]), P.tc_c[a]) : 0.f;
                 xn = __fmaf_rn(v, v, xn);
                 row[2 + 2 * a] = -2.f * v;
                 row[3 + 2 * a] = -2.f * v;

@@ -29,6 +29,8 @@
 
 namespace pakr {
 
+// Exact FP32 distance of node j to the centred query qv, from the tree's coordinates
+// (the same form and rounding as k_nn's exact_dist2), +inf if ineligible.
 template <int D>
 __device__ __forceinline__ float tc_exact(const DevProblem &P, const DevTree &T, int j, float bound, const float *qv)
 {
@@ -36,10 +38,53 @@ __device__ __forceinline__ float tc_exact(const DevProblem &P, const DevTree &T,
     float acc = 0.f;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        const float diff = __fadd_rn(qv[a], -(T.X[(size_t)a * P.cap + j] * P.sw[a]));
+        const float xc = __fsub_rn(__fmul_rn(T.X[(size_t)a * P.cap + j], P.sw[a]), P.tc_c[a]);
+        const float diff = __fadd_rn(qv[a], -xc);
         acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
     }
     return (f < bound) ? acc : __int_as_float(0x7f800000);
+}
+
+// Exact resolve of the 16-node group starting at g0 (a multiple of 16, inside one 256-node
+// tile) from the packed copy: a node's centred coordinate is hi + lo exactly (the copy keeps
+// lo = v - hi untruncated), so this equals tc_exact, and the packed tile was just streamed
+// through L2.  Four nodes at a time, their 16-byte column chunks loaded together.
+template <int D>
+__device__ __forceinline__ void tc_resolve_group(const DevTree &T, int g0, int end, float bound, const float *qv,
+                                                 float &best, int &bidx)
+{
+    using S = TcShape<D>;
+    constexpr int NC = (2 * D + 3) / 4;  // 16-byte chunks holding x_hi and x_lo of a row
+    const unsigned char *tile = reinterpret_cast<const unsigned char *>(T.XT) + (size_t)(g0 / kTcN) * S::TILE_BYTES;
+    const int r0 = g0 % kTcN;
+#pragma unroll 1
+    for (int q4 = 0; q4 < kTcG; q4 += 4) {
+        float4 ch[4][NC];
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                ch[g][c] = *reinterpret_cast<const float4 *>(tile + tc_off<D>(r0 + q4 + g, 4 * c));
+        const float4 f4 = *reinterpret_cast<const float4 *>(T.fcost + g0 + q4);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const float *row = reinterpret_cast<const float *>(ch[g]);
+            float acc = 0.f;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const float xc = __fadd_rn(row[a], row[D + a]);
+                const float diff = __fadd_rn(qv[a], -xc);
+                acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
+            }
+            const float f = g == 0 ? f4.x : g == 1 ? f4.y : g == 2 ? f4.z : f4.w;
+            const int j = g0 + q4 + g;
+            const float ex = (f < bound) ? acc : __int_as_float(0x7f800000);
+            if (j < end && (ex < best || (ex == best && j < bidx))) {
+                best = ex;
+                bidx = j;
+            }
+        }
+    }
 }
 
 // grid (chunks, ceil(K / 128)), kTcThreads threads, TcShape<D>::SMEM_REQ dynamic shared memory.
@@ -230,9 +275,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         float qc2 = 0.f;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            qv[a] = (qid < K) ? W.xr[(size_t)a * K + qid] * P.sw[a] : 0.f;
-            const float d = qv[a] - P.tc_c[a];
-            qc2 = __fmaf_rn(d, d, qc2);
+            qv[a] = (qid < K) ? __fsub_rn(__fmul_rn(W.xr[(size_t)a * K + qid], P.sw[a]), P.tc_c[a]) : 0.f;
+            qc2 = __fmaf_rn(qv[a], qv[a], qc2);
         }
         const float Rq = sqrtf(qc2) * 1.0001f + sqrtf(P.tc_xbox2);
         band = 2.f * tc_bound_coef<D>() * Rq * Rq;
@@ -308,7 +352,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const float m1f = fminf(m1, s_m1[qrow]);
         if (m1f < kTcEligible) {
             const float thrf = m1f + band;
-            const bool vec_ok = (P.cap & 3) == 0;  // 16-byte loads need 16-byte aligned rows
             if (!(ovf || s_ovf[qrow])) {
                 float best = __int_as_float(0x7f800000);
                 int bidx = 0x7FFFFFFF;
@@ -320,57 +363,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     for (int s = 0; s < np; ++s) {
                         if (!(ring_val[s * kTcReaders + owner] <= thrf))
                             continue;
-                        const int g0 = ring_grp[s * kTcReaders + owner];
-                        if (vec_ok && g0 + kTcG <= P.cap) {
-#pragma unroll
-                            for (int hb = 0; hb < kTcG; hb += 8) {
-                                float4 xf[D + 1][2];
-#pragma unroll
-                                for (int a = 0; a < D; ++a) {
-                                    const float4 *src =
-                                        reinterpret_cast<const float4 *>(T.X + (size_t)a * P.cap + g0 + hb);
-                                    xf[a][0] = src[0];
-                                    xf[a][1] = src[1];
-                                }
-                                xf[D][0] = reinterpret_cast<const float4 *>(T.fcost + g0 + hb)[0];
-                                xf[D][1] = reinterpret_cast<const float4 *>(T.fcost + g0 + hb)[1];
-#pragma unroll
-                                for (int g = 0; g < 8; ++g) {
-                                    float acc = 0.f;
-#pragma unroll
-                                    for (int a = 0; a < D; ++a) {
-                                        const float4 w = xf[a][g >> 2];
-                                        const float x = (g & 3) == 0 ? w.x : (g & 3) == 1 ? w.y : (g & 3) == 2 ? w.z : w.w;
-                                        const float diff = __fadd_rn(qv[a], -(x * P.sw[a]));
-                                        acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
-                                    }
-                                    const float4 wf = xf[D][g >> 2];
-                                    const float f = (g & 3) == 0 ? wf.x : (g & 3) == 1 ? wf.y : (g & 3) == 2 ? wf.z : wf.w;
-                                    const int j = g0 + hb + g;
-                                    const float ex = (f < bound) ? acc : __int_as_float(0x7f800000);
-                                    if (j < end && (ex < best || (ex == best && j < bidx))) {
-                                        best = ex;
-                                        bidx = j;
-                                    }
-                                }
-                            }
-                        } else {
-#pragma unroll
-                            for (int hb = 0; hb < kTcG; hb += 8) {
-                                float ex[8];
-#pragma unroll
-                                for (int g = 0; g < 8; ++g)  // indices clamped into range so all loads issue together
-                                    ex[g] = tc_exact<D>(P, T, min(g0 + hb + g, end - 1), bound, qv);
-#pragma unroll
-                                for (int g = 0; g < 8; ++g) {
-                                    const int j = g0 + hb + g;
-                                    if (j < end && (ex[g] < best || (ex[g] == best && j < bidx))) {
-                                        best = ex[g];
-                                        bidx = j;
-                                    }
-                                }
-                            }
-                        }
+                        tc_resolve_group<D>(T, ring_grp[s * kTcReaders + owner], end, bound, qv, best, bidx);
                     }
                 }
                 if (best < __int_as_float(0x7f800000))
@@ -393,7 +386,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             s_flag_qid[slot] = q;
 #pragma unroll
             for (int a = 0; a < D; ++a)
-                s_flag_q[slot][a] = W.xr[(size_t)a * K + q] * P.sw[a];
+                s_flag_q[slot][a] = __fsub_rn(__fmul_rn(W.xr[(size_t)a * K + q], P.sw[a]), P.tc_c[a]);
         }
     }
     __syncthreads();

@@ -6,8 +6,10 @@
 // with c the centre of the weighted state box.  a + |q - c|^2 is the squared
 // distance, so within one query a orders nodes like the distance.  Operands are
 // FP32 values split into TF32 parts v = hi + lo (hi = v with the low 13
-// mantissa bits cleared, lo = the same truncation of v - hi); the product is
-// formed from hi.hi + hi.lo + lo.hi, and |x - c|^2 enters as hi + lo times 1.
+// mantissa bits cleared, lo = v - hi; the query operand truncates lo the same
+// way, the packed node copy keeps it exact so that hi + lo gives v back, and
+// the tensor core reads it as TF32); the product is formed from
+// hi.hi + hi.lo + lo.hi, and |x - c|^2 enters as hi + lo times 1.
 // One tcgen05.mma of kind::tf32 with K = 8 covers two coordinates' worth of
 // those columns; a node row has KT = 3d + 2 columns rounded up to a multiple of 8.
 #pragma once
@@ -248,7 +250,7 @@ __device__ __forceinline__ void tc_pack_node(const DevProblem &P, const DevTree 
         xn = __fmaf_rn(v, v, xn);
         const float hi = tf32_trunc(v);
         row[a] = hi;
-        row[D + a] = tf32_trunc(v - hi);
+        row[D + a] = v - hi;  // exact; the tensor core reads it as TF32, the exact resolve adds it to hi
         row[2 * D + a] = hi;
     }
     const float nh = tf32_trunc(xn);
