@@ -18,10 +18,14 @@
 //
 // Roles (14 warps, one CTA per SM: it allocates all 512 TMEM columns):
 //   warp 0 lane 0   bulk-copies packed node tiles (T.XT) and f-costs into a ring of stages;
-//   warps 1-4       mask ineligible rows (|x|^2 columns := 2^100), wait for the accumulator
-//                   the tile will use to be released, then signal "tile ready";
-//   warp 5 lane 0   waits "tile ready" and issues KT/8 MMAs (M 128, N 256, K 8) per tile;
+//   warps 1-4       mask ineligible rows (|x|^2 columns := 2^100), then signal "tile masked";
+//   warp 5 lane 0   waits "tile masked" and the release of the accumulator the tile will use
+//                   (tile t - 2's), then issues KT/8 MMAs (M 128, N 256, K 8);
 //   warps 6-13      read the accumulators (tcgen05.ld), group minima, candidate rings.
+// The accumulator release goes straight to the MMA thread: every mbarrier hand-off costs
+// on the order of a hundred cycles, and the chain MMA -> readers -> MMA bounds the rate at
+// which the two accumulators turn over.  Warps off that chain wait with the suspending
+// mbarrier.try_wait, so that their polls take no issue slots from the readers.
 // Every wait is bounded (1 s of device time); on timeout the CTA sets ERR_TC_TIMEOUT,
 // stops issuing work and still frees its TMEM.
 #include "pakr_device.cuh"
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const uint32_t sB = smem_u32(sB0), sF = smem_u32(sF0);
             for (int t = 0; t < ntiles && !s_abort; ++t) {
                 const int b = t % NST;
-                if (t >= NST && !mbar_wait_bounded(smem_u32(&s_free[b]), ((t - NST) / NST) & 1, kWaitNs)) {
+                if (t >= NST && !mbar_wait_suspend(smem_u32(&s_free[b]), ((t - NST) / NST) & 1, kWaitNs)) {
                     s_abort = 1;
                     atomicOr(&ctl->err, ERR_TC_TIMEOUT);
                     break;
@@ -217,12 +221,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int r0 = tid - kTcPatch0 * 32;  // rows r0 and r0 + 128 of every tile
         for (int t = 0; t < ntiles; ++t) {
             const int b = t % NST;
-            const bool ok = !s_abort && mbar_wait_bounded(smem_u32(&s_loaded[b]), (t / NST) & 1, kWaitNs);
+            const bool ok = !s_abort && mbar_wait_suspend(smem_u32(&s_loaded[b]), (t / NST) & 1, kWaitNs);
             if (!ok && !s_abort) {
                 s_abort = 1;
                 atomicOr(&ctl->err, ERR_TC_TIMEOUT);
             }
             if (ok) {
+                bool wrote = false;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int r = r0 + 128 * h;
@@ -231,41 +236,43 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         unsigned char *rowp = sB0 + b * S::TILE_BYTES;
                         *reinterpret_cast<float *>(rowp + tc_off<D>(r, 3 * D)) = kTcSentinel;
                         *reinterpret_cast<float *>(rowp + tc_off<D>(r, 3 * D + 1)) = 0.f;
+                        wrote = true;
                     }
                 }
-                fence_async_smem();
+                if (wrote)
+                    fence_async_smem();
             }
             __syncwarp();
-            if (lane == 0) {
-                // "tile ready" also means the accumulator it will use (tile t - 2's) has been read
-                if (ok && t >= kTcAcc && !s_abort &&
-                    !mbar_wait_bounded(smem_u32(&s_empty[t % kTcAcc]), ((t - kTcAcc) / kTcAcc) & 1, kWaitNs)) {
-                    s_abort = 1;
-                    atomicOr(&ctl->err, ERR_TC_TIMEOUT);
-                }
+            if (lane == 0)
                 mbar_arrive(smem_u32(&s_full[b]));
-            }
         }
     } else if (warp == kTcMmaWarp) {
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_tf32(kTcM, kTcN);
-            const uint32_t a_addr = smem_u32(sA), b_addr = smem_u32(sB0);
+            // descriptors of stage 0 and k-step 0; the start-address field (address / 16, 14 bits)
+            // takes the stage and k-step offsets directly (shared addresses stay below 256 KB)
+            const uint64_t adesc = smem_desc(smem_u32(sA), S::LBO, S::SBO);
+            const uint64_t bdesc = smem_desc(smem_u32(sB0), S::LBO, S::SBO);
             // no per-tile poll of the abort flag (a shared-memory load that queues behind the
             // tile traffic): the masking warps signal every tile even after an abort, and a
-            // wait that times out ends the loop
+            // wait that times out (also the release wait, once the readers have stopped) ends
+            // the loop
             for (int t = 0; t < ntiles; ++t) {
                 const int st = t % NST, ac = t % kTcAcc;
-                if (!mbar_wait_bounded(smem_u32(&s_full[st]), (t / NST) & 1, kWaitNs)) {
+                // the tile is masked, and the accumulator it will use (tile t - 2's) has been read
+                if (!mbar_wait_bounded(smem_u32(&s_full[st]), (t / NST) & 1, kWaitNs) ||
+                    (t >= kTcAcc &&
+                     !mbar_wait_bounded(smem_u32(&s_empty[ac]), ((t - kTcAcc) / kTcAcc) & 1, kWaitNs))) {
                     s_abort = 1;
                     atomicOr(&ctl->err, ERR_TC_TIMEOUT);
                     break;
                 }
                 tc_fence_after();
+                const uint64_t bd = bdesc + (uint64_t)((st * S::TILE_BYTES) >> 4);
 #pragma unroll
                 for (int s = 0; s < KT / 8; ++s)
-                    mma_tf32_ss(tbase + (uint32_t)(ac * kTcN), smem_desc(a_addr + 2 * S::LBO * s, S::LBO, S::SBO),
-                                smem_desc(b_addr + st * S::TILE_BYTES + 2 * S::LBO * s, S::LBO, S::SBO), idesc,
-                                s > 0 ? 1u : 0u);
+                    mma_tf32_ss(tbase + (uint32_t)(ac * kTcN), adesc + (uint64_t)((2 * S::LBO * s) >> 4),
+                                bd + (uint64_t)((2 * S::LBO * s) >> 4), idesc, s > 0 ? 1u : 0u);
                 mma_commit(smem_u32(&s_free[st]));
                 mma_commit(smem_u32(&s_done[ac]));
             }
@@ -284,7 +291,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int t = 0; t < ntiles; ++t) {
             const int b = t % kTcAcc;
             const bool ok =
-                __all_sync(0xFFFFFFFFu, mbar_wait_bounded(smem_u32(&s_done[b]), (t / kTcAcc) & 1, kWaitNs));
+                __all_sync(0xFFFFFFFFu, mbar_wait_suspend(smem_u32(&s_done[b]), (t / kTcAcc) & 1, kWaitNs));
             if (!ok) {
                 if (lane == 0) {
                     s_abort = 1;
@@ -295,39 +302,44 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             tc_fence_after();
             const uint32_t tcol = tbase + (uint32_t)(b * kTcN + 128 * half) + ((uint32_t)(32 * quarter) << 16);
             const int gbase = start + t * kTcN + 128 * half;
-#pragma unroll 1
-            for (int c = 0; c < 2; ++c) {
+            // minima of this row's eight 16-node groups: two 64-column loads, the accumulator is
+            // released after the second; one branch per tile (the candidate test rarely passes
+            // once the running minimum has settled, and a branch per group would stall the warp
+            // on every minimum tree)
+            float m[8];
+            {
                 float v[64];
                 __syncwarp();
-                tmem_ld64(tcol + 64 * c, v);
-                if (c == 1) {
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0)
-                        mbar_arrive(smem_u32(&s_empty[b]));
-                }
-                float m[4];
+                tmem_ld64(tcol, v);
 #pragma unroll
                 for (int h4 = 0; h4 < 4; ++h4)
                     m[h4] = min16(v + 16 * h4);
+                __syncwarp();
+                tmem_ld64(tcol + 64, v);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(smem_u32(&s_empty[b]));
 #pragma unroll
-                for (int h4 = 0; h4 < 4; ++h4) {
-                    if (m[h4] <= thr) {
-                        if (m[h4] < m1) {
-                            m1 = m[h4];
+                for (int h4 = 0; h4 < 4; ++h4)
+                    m[4 + h4] = min16(v + 16 * h4);
+            }
+            const float mm = fminf(fmin3(m[0], m[1], m[2]), fmin3(m[3], fmin3(m[4], m[5], m[6]), m[7]));
+            if (mm <= thr) {
+#pragma unroll
+                for (int h8 = 0; h8 < 8; ++h8) {
+                    if (m[h8] <= thr) {
+                        if (m[h8] < m1) {
+                            m1 = m[h8];
                             thr = m1 + band;
                         }
                         const int slot = pos & (kTcRing - 1);
                         // an entry still within the band would be lost: the row falls back to a rescan
                         if (pos >= kTcRing && ring_val[slot * kTcReaders + e] <= thr)
                             ovf = 1;
-                        const int g0 = gbase + 64 * c + 16 * h4;
-                        ring_val[slot * kTcReaders + e] = m[h4];
-                        ring_grp[slot * kTcReaders + e] = g0;
+                        ring_val[slot * kTcReaders + e] = m[h8];
+                        ring_grp[slot * kTcReaders + e] = gbase + 16 * h8;
                         ++pos;
-#pragma unroll
-                        for (int a = 0; a < D; ++a)
-                            asm volatile("prefetch.global.L2 [%0];" ::"l"(T.X + (size_t)a * P.cap + g0));
                     }
                 }
             }

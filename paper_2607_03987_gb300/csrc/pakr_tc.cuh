@@ -86,6 +86,34 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
             return false;
     }
 }
+// Potentially blocking test of the phase: the thread is suspended until the phase
+// completes or a hardware time limit passes, so a waiting warp issues nothing.
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Wait for the phase for at most limit_ns of device time without spinning: for the warps
+// that are not on the tensor pipe's critical path, whose polls would take issue slots and
+// ALU cycles from the accumulator readers on the same scheduler.
+__device__ __forceinline__ bool mbar_wait_suspend(uint32_t bar, uint32_t parity, unsigned long long limit_ns)
+{
+    if (mbar_test_wait(bar, parity))
+        return true;
+    const unsigned long long t0 = tc_clock_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity))
+            return true;
+        if (tc_clock_ns() - t0 > limit_ns)
+            return false;
+    }
+}
 // D[tmem] (+)= A[smem] * B[smem]^T, kind::tf32, one CTA.
 __device__ __forceinline__ void mma_tf32_ss(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                             uint32_t accumulate)
