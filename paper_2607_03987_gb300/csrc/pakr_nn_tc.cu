@@ -91,6 +91,24 @@ __device__ __forceinline__ void tc_resolve_group(const DevTree &T, int g0, int e
     }
 }
 
+// Bring the packed rows and f-costs of the 16-node group starting at g0 into L2: two 8-row
+// core-matrix groups, each (2d + 3) / 4 16-byte chunks wide (128-byte lines), and one line
+// of f-costs.
+template <int D>
+__device__ __forceinline__ void tc_prefetch_group(const DevTree &T, int g0)
+{
+    using S = TcShape<D>;
+    constexpr int NC = (2 * D + 3) / 4;
+    const unsigned char *tile = reinterpret_cast<const unsigned char *>(T.XT) + (size_t)(g0 / kTcN) * S::TILE_BYTES;
+    const int r0 = g0 % kTcN;
+#pragma unroll
+    for (int rg = 0; rg < 2; ++rg)
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(tile + tc_off<D>(r0 + 8 * rg, 4 * c)));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(T.fcost + g0));
+}
+
 // grid (chunks, ceil(K / 128)), kTcThreads threads, TcShape<D>::SMEM_REQ dynamic shared memory.
 // T.fcost must be readable 4 floats past the node count (the f-cost copy rounds up to 16 bytes).
 template <int D>
@@ -257,24 +275,37 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // tile traffic): the masking warps signal every tile even after an abort, and a
             // wait that times out (also the release wait, once the readers have stopped) ends
             // the loop
+            // the loop keeps its bookkeeping to a few instructions: this thread shares its
+            // scheduler with two readers that keep the ALU busy
+            const uint32_t full0 = smem_u32(&s_full[0]), free0 = smem_u32(&s_free[0]);
+            const uint32_t done0 = smem_u32(&s_done[0]), empty0 = smem_u32(&s_empty[0]);
+            uint32_t st8 = 0, fpar = 0;  // stage * 8 (mbarrier byte offset), its phase parity
+            uint64_t bd = bdesc;
             for (int t = 0; t < ntiles; ++t) {
-                const int st = t % NST, ac = t % kTcAcc;
+                const uint32_t ac = (uint32_t)t & 1u;
                 // the tile is masked, and the accumulator it will use (tile t - 2's) has been read
-                if (!mbar_wait_bounded(smem_u32(&s_full[st]), (t / NST) & 1, kWaitNs) ||
-                    (t >= kTcAcc &&
-                     !mbar_wait_bounded(smem_u32(&s_empty[ac]), ((t - kTcAcc) / kTcAcc) & 1, kWaitNs))) {
+                if (!mbar_wait_bounded(full0 + st8, fpar, kWaitNs) ||
+                    (t >= kTcAcc && !mbar_wait_bounded(empty0 + 8 * ac, (((uint32_t)t >> 1) + 1u) & 1u, kWaitNs))) {
                     s_abort = 1;
                     atomicOr(&ctl->err, ERR_TC_TIMEOUT);
                     break;
                 }
                 tc_fence_after();
-                const uint64_t bd = bdesc + (uint64_t)((st * S::TILE_BYTES) >> 4);
+                const uint32_t dt = tbase + ac * (uint32_t)kTcN;
+                mma_tf32_ss_c<false>(dt, adesc, bd, idesc);
 #pragma unroll
-                for (int s = 0; s < KT / 8; ++s)
-                    mma_tf32_ss(tbase + (uint32_t)(ac * kTcN), adesc + (uint64_t)((2 * S::LBO * s) >> 4),
-                                bd + (uint64_t)((2 * S::LBO * s) >> 4), idesc, s > 0 ? 1u : 0u);
-                mma_commit(smem_u32(&s_free[st]));
-                mma_commit(smem_u32(&s_done[ac]));
+                for (int s = 1; s < KT / 8; ++s)
+                    mma_tf32_ss_c<true>(dt, adesc + (uint64_t)((2 * S::LBO * s) >> 4),
+                                        bd + (uint64_t)((2 * S::LBO * s) >> 4), idesc);
+                mma_commit(free0 + st8);
+                mma_commit(done0 + 8 * ac);
+                st8 += 8;
+                bd += (uint64_t)(S::TILE_BYTES >> 4);
+                if (st8 == 8 * NST) {
+                    st8 = 0;
+                    fpar ^= 1u;
+                    bd = bdesc;
+                }
             }
         }
         __syncwarp();
@@ -365,6 +396,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (m1f < kTcEligible) {
             const float thrf = m1f + band;
             if (!(ovf || s_ovf[qrow])) {
+                // every CTA resolves at the same moment, and the streamed tiles have mostly left
+                // L2 by now: request all surviving groups' lines first, so that their DRAM round
+                // trips overlap instead of following one another group by group
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) {
+                    const int owner = e + 128 * h;
+                    const int np = min(h == 0 ? pos : s_pos[qrow], kTcRing);
+#pragma unroll 1
+                    for (int s = 0; s < np; ++s)
+                        if (ring_val[s * kTcReaders + owner] <= thrf)
+                            tc_prefetch_group<D>(T, ring_grp[s * kTcReaders + owner]);
+                }
                 float best = __int_as_float(0x7f800000);
                 int bidx = 0x7FFFFFFF;
 #pragma unroll 1
