@@ -812,14 +812,15 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
     C.nn_qgroups = (p->K + per_block - 1) / per_block;
     const int occ = std::max(1, nn_blocks_per_sm(di.d, C.nn_variant));
     C.nn_chunks = std::max(1, sms * occ / C.nn_qgroups);
-    // tensor-core grid: one CTA per SM; node chunks x query blocks in near-full waves of the SMs
+    // tensor-core grid: kTcCtasPerSm CTAs per SM; node chunks x query blocks in near-full waves
     C.tc_qblocks = (p->K + 127) / 128;  // 128 queries per tensor-core CTA
-    C.tc_chunks = std::max(1, sms / C.tc_qblocks);
+    const int tc_slots = sms * kTcCtasPerSm;
+    C.tc_chunks = std::max(1, tc_slots / C.tc_qblocks);
     for (int w = 1; w <= 16; ++w) {
-        const int c = (w * sms + C.tc_qblocks - 1) / C.tc_qblocks;
+        const int c = (w * tc_slots + C.tc_qblocks - 1) / C.tc_qblocks;
         const int items = c * C.tc_qblocks;
-        const int waves = (items + sms - 1) / sms;
-        if ((double)items / ((double)waves * sms) >= 0.95) {
+        const int waves = (items + tc_slots - 1) / tc_slots;
+        if ((double)items / ((double)waves * tc_slots) >= 0.95) {
             C.tc_chunks = c;
             break;
         }

@@ -19,6 +19,7 @@ enum { COST_PATH_LENGTH = 0, COST_DURATION = 1 };
 enum { H_POSITION = 0, H_FULLSTATE = 1 };
 enum { MODE_EXPAND = 0, MODE_PLAN = 1 };
 enum { ERR_PATH_CYCLE = 1, ERR_BAD_PARENT = 2, ERR_TC_TIMEOUT = 4 };
+constexpr int kTcCtasPerSm = 2;  // resident tensor-core nearest-neighbour CTAs per SM
 
 // Problem constants, passed to every kernel by value.
 struct DevProblem {

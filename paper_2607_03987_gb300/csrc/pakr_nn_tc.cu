@@ -4,30 +4,33 @@
 // Sec. IV-A, IV-B): for each query the eligible node (f-cost below the bound)
 // with the smallest exact FP32 squared distance, the lowest index on a tie.
 //
-// A CTA takes 128 queries (one query block) and a chunk of whole 256-node tiles.
-// Per tile the tensor cores compute the filter a = |x - c|^2 - 2 (q - c).(x - c)
-// for all 128 x 256 pairs into TMEM; reader warps take each row's minimum over
-// groups of 16 nodes and remember the groups whose minimum lies within `band`
-// of the row's running minimum (band = 2 * B, B the bound of tc_bound_coef on
-// |a + |q - c|^2 - e|).  After the chunk, every node whose exact distance could
-// be the row's minimum lies in a remembered group (its filter value is at most
-// m1 + band), so recomputing e on those groups gives the exact argmin.  A row
-// whose candidate ring overflowed, or a tree flagged as leaving the box bound,
-// is rescanned exactly by the whole CTA.  Chunk results merge with a 64-bit
-// atomicMin of (distance bits << 32 | index), as in k_nn.
+// A CTA takes 128 queries (one query block) and a chunk of whole 128-node half tiles of the
+// packed operand copy.  Per half tile the tensor cores compute the filter
+// a = |x - c|^2 - 2 (q - c).(x - c) for all 128 x 128 pairs into TMEM; reader warps take
+// each row's minimum over groups of 16 nodes and remember the groups whose minimum lies
+// within `band` of the row's running minimum (band = 2 * B, B the bound of tc_bound_coef on
+// |a + |q - c|^2 - e|).  After the chunk, every node whose exact distance could be the
+// row's minimum lies in a remembered group (its filter value is at most m1 + band), so
+// recomputing e on those groups gives the exact argmin.  A row whose candidate ring
+// overflowed, or a tree flagged as leaving the box bound, is rescanned exactly by the whole
+// CTA.  Chunk results merge with a 64-bit atomicMin of (distance bits << 32 | index), as in
+// k_nn.
 //
-// Roles (14 warps, one CTA per SM: it allocates all 512 TMEM columns):
-//   warp 0 lane 0   bulk-copies packed node tiles (T.XT) and f-costs into a ring of stages;
-//   warps 1-4       mask ineligible rows (|x|^2 columns := 2^100), then signal "tile masked";
-//   warp 5 lane 0   waits "tile masked" and the release of the accumulator the tile will use
-//                   (tile t - 2's), then issues KT/8 MMAs (M 128, N 256, K 8);
-//   warps 6-13      read the accumulators (tcgen05.ld), group minima, candidate rings.
-// The accumulator release goes straight to the MMA thread: every mbarrier hand-off costs
-// on the order of a hundred cycles, and the chain MMA -> readers -> MMA bounds the rate at
-// which the two accumulators turn over.  Warps off that chain wait with the suspending
-// mbarrier.try_wait, so that their polls take no issue slots from the readers.
-// Every wait is bounded (1 s of device time); on timeout the CTA sets ERR_TC_TIMEOUT,
-// stops issuing work and still frees its TMEM.
+// Two CTAs share an SM, each with two accumulators of 128 TMEM columns.  Within a CTA the
+// work is one dependency chain (MMA, commit, readers, release, next MMA) whose mbarrier
+// hand-offs cost on the order of a hundred cycles each; the second CTA's MMAs fill the
+// tensor pipe while the first waits on that chain.
+//
+// Roles (8 warps per CTA):
+//   warp 0 lane 0   bulk-copies packed half tiles (T.XT) and f-costs into a ring of stages;
+//   warp 1 lane 0   waits "stage masked" and the release of the accumulator the tile will use
+//                   (tile t - 2's), then issues KT/8 MMAs (M 128, N 128, K 8);
+//   warps 2-3       mask ineligible rows (|x|^2 columns := 2^100), then signal "stage masked";
+//   warps 4-7       read the accumulators (two 64-column tcgen05.ld per tile), group minima,
+//                   candidate rings; one reader thread per query row.
+// Warps off the MMA thread's chain wait with the suspending mbarrier.try_wait, so that their
+// polls take no issue slots from the readers.  Every wait is bounded (1 s of device time);
+// on timeout the CTA sets ERR_TC_TIMEOUT, stops issuing work and still frees its TMEM.
 #include "pakr_device.cuh"
 #include "pakr_tc.cuh"
 
@@ -109,10 +112,11 @@ __device__ __forceinline__ void tc_prefetch_group(const DevTree &T, int g0)
     asm volatile("prefetch.global.L2 [%0];" ::"l"(T.fcost + g0));
 }
 
-// grid (chunks, ceil(K / 128)), kTcThreads threads, TcShape<D>::SMEM_REQ dynamic shared memory.
-// T.fcost must be readable 4 floats past the node count (the f-cost copy rounds up to 16 bytes).
+// grid (chunks, ceil(K / 128)), kTcThreads threads, TcShape<D>::SMEM_REQ dynamic shared memory;
+// two CTAs per SM.  T.fcost must be readable 4 floats past the node count (the f-cost copy
+// rounds up to 16 bytes).
 template <int D>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
     k_nn_tc(DevProblem P, Ctl *__restrict__ ctl, DevTree T, DevWork W)
 {
     using S = TcShape<D>;
@@ -121,29 +125,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char *sA = tc_smem;
     unsigned char *sB0 = tc_smem + S::A_BYTES;
-    float *sF0 = reinterpret_cast<float *>(tc_smem + S::A_BYTES + NST * S::TILE_BYTES);
-    float *ring_val = reinterpret_cast<float *>(tc_smem + S::A_BYTES + NST * (S::TILE_BYTES + S::F_BYTES));
+    float *sF0 = reinterpret_cast<float *>(tc_smem + S::A_BYTES + NST * S::STAGE_BYTES);
+    float *ring_val = reinterpret_cast<float *>(tc_smem + S::A_BYTES + NST * (S::STAGE_BYTES + S::F_BYTES));
     int *ring_grp = reinterpret_cast<int *>(ring_val + kTcRing * kTcReaders);
     __shared__ __align__(8) unsigned long long s_loaded[NST], s_full[NST], s_free[NST];
     __shared__ __align__(8) unsigned long long s_done[kTcAcc], s_empty[kTcAcc];
     __shared__ uint32_t s_tbase;
     __shared__ volatile int s_abort;
-    __shared__ float s_m1[kTcM];
-    __shared__ int s_pos[kTcM], s_ovf[kTcM];
     __shared__ int s_nflag, s_flag_qid[kTcM];
     __shared__ float s_flag_q[kTcM][D];
 
     const int n = ctl->n_start;
     if (n < P.tc_min_n)
         return;  // small trees take k_nn
-    const int ntile_all = (n + kTcN - 1) / kTcN;
+    // the chunk: whole half tiles of 128 nodes
+    const int ntile_all = (n + kTcBN - 1) / kTcBN;
     const int tiles_per = (ntile_all + gridDim.x - 1) / gridDim.x;
     const int tile0 = blockIdx.x * tiles_per;
     const int ntiles = min(ntile_all, tile0 + tiles_per) - tile0;
     if (ntiles <= 0)
         return;
-    const int start = tile0 * kTcN;
-    const int end = min(n, start + ntiles * kTcN);
+    const int start = tile0 * kTcBN;
+    const int end = min(n, start + ntiles * kTcBN);
     const float bound = ctl->bound;
     const bool flagged = ctl->tc_flag != 0;
     const int K = P.K;
@@ -153,14 +156,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     // ---- setup: TMEM, barriers, the query operand ----
     if (warp == kTcMmaWarp) {
-        tmem_alloc(smem_u32(&s_tbase), 512);
+        tmem_alloc(smem_u32(&s_tbase), kTcCols);
         tmem_relinquish();
     }
     if (tid == 0) {
 #pragma unroll
         for (int i = 0; i < NST; ++i) {
             mbar_init(smem_u32(&s_loaded[i]), 1);
-            mbar_init(smem_u32(&s_full[i]), 4);
+            mbar_init(smem_u32(&s_full[i]), 2);
             mbar_init(smem_u32(&s_free[i]), 1);
         }
 #pragma unroll
@@ -202,10 +205,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     const uint32_t tbase = s_tbase;
 
-    // reader state
-    const int e = tid - kTcReader0 * 32;
-    const int quarter = warp & 3, half = (warp - kTcReader0) >> 2;
+    // reader state: one reader thread per query row
+    const int quarter = warp & 3;
     const int qrow = 32 * quarter + lane;
+    const int e = qrow;  // ring column
     const int qid = qbase + qrow;
     float qv[D];
     float m1 = kTcEligible;
@@ -224,19 +227,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     atomicOr(&ctl->err, ERR_TC_TIMEOUT);
                     break;
                 }
-                const int j0 = start + t * kTcN;
-                const uint32_t fbytes = (uint32_t)(((min(kTcN, end - j0) + 3) & ~3) * 4);
+                const int h = tile0 + t;  // global half-tile index
+                const int j0 = h * kTcBN;
+                const uint32_t fbytes = (uint32_t)(((min(kTcBN, end - j0) + 3) & ~3) * 4);
                 const uint32_t bar = smem_u32(&s_loaded[b]);
-                mbar_arrive_expect_tx(bar, (uint32_t)S::TILE_BYTES + fbytes);
-                bulk_g2s(sB + b * S::TILE_BYTES,
-                         reinterpret_cast<const unsigned char *>(T.XT) + (size_t)(tile0 + t) * S::TILE_BYTES,
-                         S::TILE_BYTES, bar);
+                mbar_arrive_expect_tx(bar, (uint32_t)S::STAGE_BYTES + fbytes);
+                bulk_g2s(sB + b * S::STAGE_BYTES,
+                         reinterpret_cast<const unsigned char *>(T.XT) + (size_t)(h >> 1) * S::TILE_BYTES +
+                             (size_t)(h & 1) * S::STAGE_BYTES,
+                         S::STAGE_BYTES, bar);
                 bulk_g2s(sF + b * S::F_BYTES, T.fcost + j0, fbytes, bar);
             }
         }
         __syncwarp();
-    } else if (warp >= kTcPatch0 && warp < kTcPatch0 + 4) {
-        const int r0 = tid - kTcPatch0 * 32;  // rows r0 and r0 + 128 of every tile
+    } else if (warp >= kTcPatch0 && warp < kTcReader0) {
+        const int r0 = tid - kTcPatch0 * 32;  // rows r0 and r0 + 64 of every stage
         for (int t = 0; t < ntiles; ++t) {
             const int b = t % NST;
             const bool ok = !s_abort && mbar_wait_suspend(smem_u32(&s_loaded[b]), (t / NST) & 1, kWaitNs);
@@ -248,10 +253,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 bool wrote = false;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int r = r0 + 128 * h;
-                    const int j = start + t * kTcN + r;
-                    if (!(j < end && sF0[b * kTcN + r] < bound)) {
-                        unsigned char *rowp = sB0 + b * S::TILE_BYTES;
+                    const int r = r0 + 64 * h;
+                    const int j = start + t * kTcBN + r;
+                    if (!(j < end && sF0[b * kTcBN + r] < bound)) {
+                        unsigned char *rowp = sB0 + b * S::STAGE_BYTES;
                         *reinterpret_cast<float *>(rowp + tc_off<D>(r, 3 * D)) = kTcSentinel;
                         *reinterpret_cast<float *>(rowp + tc_off<D>(r, 3 * D + 1)) = 0.f;
                         wrote = true;
@@ -266,24 +271,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
     } else if (warp == kTcMmaWarp) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_tf32(kTcM, kTcN);
+            constexpr uint32_t idesc = idesc_tf32(kTcM, kTcBN);
             // descriptors of stage 0 and k-step 0; the start-address field (address / 16, 14 bits)
             // takes the stage and k-step offsets directly (shared addresses stay below 256 KB)
             const uint64_t adesc = smem_desc(smem_u32(sA), S::LBO, S::SBO);
             const uint64_t bdesc = smem_desc(smem_u32(sB0), S::LBO, S::SBO);
             // no per-tile poll of the abort flag (a shared-memory load that queues behind the
-            // tile traffic): the masking warps signal every tile even after an abort, and a
+            // tile traffic): the masking warps signal every stage even after an abort, and a
             // wait that times out (also the release wait, once the readers have stopped) ends
             // the loop
-            // the loop keeps its bookkeeping to a few instructions: this thread shares its
-            // scheduler with two readers that keep the ALU busy
             const uint32_t full0 = smem_u32(&s_full[0]), free0 = smem_u32(&s_free[0]);
             const uint32_t done0 = smem_u32(&s_done[0]), empty0 = smem_u32(&s_empty[0]);
             uint32_t st8 = 0, fpar = 0;  // stage * 8 (mbarrier byte offset), its phase parity
             uint64_t bd = bdesc;
             for (int t = 0; t < ntiles; ++t) {
                 const uint32_t ac = (uint32_t)t & 1u;
-                // the tile is masked, and the accumulator it will use (tile t - 2's) has been read
+                // the stage is masked, and the accumulator it will use (tile t - 2's) has been read
                 if (!mbar_wait_bounded(full0 + st8, fpar, kWaitNs) ||
                     (t >= kTcAcc && !mbar_wait_bounded(empty0 + 8 * ac, (((uint32_t)t >> 1) + 1u) & 1u, kWaitNs))) {
                     s_abort = 1;
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dt = tbase + ac * (uint32_t)kTcN;
+                const uint32_t dt = tbase + ac * (uint32_t)kTcBN;
                 mma_tf32_ss_c<false>(dt, adesc, bd, idesc);
 #pragma unroll
                 for (int s = 1; s < KT / 8; ++s)
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 mma_commit(free0 + st8);
                 mma_commit(done0 + 8 * ac);
                 st8 += 8;
-                bd += (uint64_t)(S::TILE_BYTES >> 4);
+                bd += (uint64_t)(S::STAGE_BYTES >> 4);
                 if (st8 == 8 * NST) {
                     st8 = 0;
                     fpar ^= 1u;
@@ -331,8 +334,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 break;
             }
             tc_fence_after();
-            const uint32_t tcol = tbase + (uint32_t)(b * kTcN + 128 * half) + ((uint32_t)(32 * quarter) << 16);
-            const int gbase = start + t * kTcN + 128 * half;
+            const uint32_t tcol = tbase + (uint32_t)(b * kTcBN) + ((uint32_t)(32 * quarter) << 16);
+            const int gbase = start + t * kTcBN;
             // minima of this row's eight 16-node groups: two 64-column loads, the accumulator is
             // released after the second; one branch per tile (the candidate test rarely passes
             // once the running minimum has settled, and a branch per group would stall the warp
@@ -375,62 +378,45 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
             }
         }
-        if (half == 1) {
-            s_m1[qrow] = m1;
-            s_pos[qrow] = pos;
-            s_ovf[qrow] = ovf;
-        }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == kTcMmaWarp) {
         tc_fence_after();
-        tmem_dealloc(tbase, 512);
+        tmem_dealloc(tbase, kTcCols);
     }
     if (s_abort)
         return;
 
-    // ---- exact resolve of the candidate groups (both column halves of the row) ----
-    if (!flagged && warp >= kTcReader0 && half == 0 && qid < K) {
-        const float m1f = fminf(m1, s_m1[qrow]);
-        if (m1f < kTcEligible) {
-            const float thrf = m1f + band;
-            if (!(ovf || s_ovf[qrow])) {
-                // every CTA resolves at the same moment, and the streamed tiles have mostly left
-                // L2 by now: request all surviving groups' lines first, so that their DRAM round
-                // trips overlap instead of following one another group by group
+    // ---- exact resolve of the candidate groups ----
+    if (!flagged && warp >= kTcReader0 && qid < K && m1 < kTcEligible) {
+        const float thrf = m1 + band;
+        if (!ovf) {
+            // every CTA resolves at the same moment, and the streamed tiles have mostly left
+            // L2 by now: request all surviving groups' lines first, so that their DRAM round
+            // trips overlap instead of following one another group by group
+            const int np = min(pos, kTcRing);
 #pragma unroll 1
-                for (int h = 0; h < 2; ++h) {
-                    const int owner = e + 128 * h;
-                    const int np = min(h == 0 ? pos : s_pos[qrow], kTcRing);
+            for (int s = 0; s < np; ++s)
+                if (ring_val[s * kTcReaders + e] <= thrf)
+                    tc_prefetch_group<D>(T, ring_grp[s * kTcReaders + e]);
+            float best = __int_as_float(0x7f800000);
+            int bidx = 0x7FFFFFFF;
 #pragma unroll 1
-                    for (int s = 0; s < np; ++s)
-                        if (ring_val[s * kTcReaders + owner] <= thrf)
-                            tc_prefetch_group<D>(T, ring_grp[s * kTcReaders + owner]);
-                }
-                float best = __int_as_float(0x7f800000);
-                int bidx = 0x7FFFFFFF;
-#pragma unroll 1
-                for (int h = 0; h < 2; ++h) {
-                    const int owner = e + 128 * h;
-                    const int np = min(h == 0 ? pos : s_pos[qrow], kTcRing);
-#pragma unroll 1
-                    for (int s = 0; s < np; ++s) {
-                        if (!(ring_val[s * kTcReaders + owner] <= thrf))
-                            continue;
-                        tc_resolve_group<D>(T, ring_grp[s * kTcReaders + owner], end, bound, qv, best, bidx);
-                    }
-                }
-                if (best < __int_as_float(0x7f800000))
-                    atomicMin(&W.nn_key[qid],
-                              ((unsigned long long)__float_as_uint(best) << 32) | (unsigned long long)(uint32_t)bidx);
-            } else {
-                const int slot = atomicAdd(&s_nflag, 1);
-                s_flag_qid[slot] = qid;
-#pragma unroll
-                for (int a = 0; a < D; ++a)
-                    s_flag_q[slot][a] = qv[a];
+            for (int s = 0; s < np; ++s) {
+                if (!(ring_val[s * kTcReaders + e] <= thrf))
+                    continue;
+                tc_resolve_group<D>(T, ring_grp[s * kTcReaders + e], end, bound, qv, best, bidx);
             }
+            if (best < __int_as_float(0x7f800000))
+                atomicMin(&W.nn_key[qid],
+                          ((unsigned long long)__float_as_uint(best) << 32) | (unsigned long long)(uint32_t)bidx);
+        } else {
+            const int slot = atomicAdd(&s_nflag, 1);
+            s_flag_qid[slot] = qid;
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+                s_flag_q[slot][a] = qv[a];
         }
     }
     if (flagged && tid < kTcM) {

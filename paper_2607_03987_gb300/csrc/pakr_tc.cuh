@@ -221,18 +221,20 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
 // Operand geometry.
 // ---------------------------------------------------------------------------
 constexpr int kTcM = 128;        // queries per CTA (MMA M)
-constexpr int kTcN = 256;        // nodes per tile (MMA N); two accumulators fill the 512 TMEM columns
-constexpr int kTcAcc = 2;
-constexpr int kTcReaders = 256;  // 8 accumulator-reader warps: two per TMEM lane quarter, one column half each
+constexpr int kTcN = 256;        // nodes per tile of the packed operand copy
+constexpr int kTcBN = 128;       // nodes per pipeline stage and MMA (N): half a packed tile
+constexpr int kTcAcc = 2;        // accumulators of kTcBN columns per CTA
+constexpr int kTcCols = kTcAcc * kTcBN;  // TMEM columns per CTA: two CTAs share an SM's 512
+constexpr int kTcReaders = 128;  // 4 accumulator-reader warps, one per TMEM lane quarter
 constexpr int kTcG = 16;         // nodes per filter group
 constexpr int kTcRing = 8;       // candidate groups remembered per (query, reader)
 constexpr float kTcSentinel = 1.2676506e30f;  // 2^100: |x - c|^2 of ineligible and padding nodes
 constexpr float kTcEligible = 6.338253e29f;   // 2^99: filter values at or above are not eligible nodes
 // warp roles
-constexpr int kTcLoadWarp = 0;   // lane 0: bulk copies of node tiles and f-costs
-constexpr int kTcPatch0 = 1;     // warps 1-4: mask ineligible rows, signal "tile ready"
-constexpr int kTcMmaWarp = 5;    // lane 0: MMAs; the warp owns the TMEM allocation
-constexpr int kTcReader0 = 6;    // warps 6-13: accumulator readers
+constexpr int kTcLoadWarp = 0;   // lane 0: bulk copies of node half tiles and f-costs
+constexpr int kTcMmaWarp = 1;    // lane 0: MMAs; the warp owns the TMEM allocation
+constexpr int kTcPatch0 = 2;     // warps 2-3: mask ineligible rows, signal "stage masked"
+constexpr int kTcReader0 = 4;    // warps 4-7: accumulator readers (warp w reads lane quarter w % 4)
 constexpr int kTcThreads = kTcReader0 * 32 + kTcReaders;
 
 template <int D>
@@ -240,14 +242,17 @@ struct TcShape {
     static constexpr int KT = ((3 * D + 2) + 7) / 8 * 8;  // x_hi, x_lo, x_hi, |x|^2 hi, lo, zero padding
     static constexpr int LBO = 128, SBO = KT * 32;         // no-swizzle K-major core-matrix layout
     static constexpr int TILE_BYTES = kTcN * KT * 4;       // one packed node tile, contiguous
+    static constexpr int STAGE_BYTES = kTcBN * KT * 4;     // half a packed tile: also contiguous
     static constexpr int A_BYTES = kTcM * KT * 4;
-    static constexpr int F_BYTES = kTcN * 4;
+    static constexpr int F_BYTES = kTcBN * 4;
     static constexpr int RING_BYTES = kTcRing * kTcReaders * 8;
-    static constexpr int NSTAGE_FIT = (200 * 1024 - A_BYTES - RING_BYTES) / (TILE_BYTES + F_BYTES);
-    static constexpr int NSTAGE = NSTAGE_FIT > 6 ? 6 : NSTAGE_FIT;  // node tiles staged in shared memory
-    static constexpr int SMEM = A_BYTES + NSTAGE * (TILE_BYTES + F_BYTES) + RING_BYTES;
-    // at least enough dynamic shared memory that a CTA holds an SM alone (it allocates all 512 TMEM columns)
-    static constexpr int SMEM_REQ = SMEM > 120 * 1024 ? SMEM : 120 * 1024;
+    // two CTAs per SM: each within half of the SM's 228 KB, static shared memory included
+    static constexpr int NSTAGE_FIT = (100 * 1024 - A_BYTES - RING_BYTES) / (STAGE_BYTES + F_BYTES);
+    static constexpr int NSTAGE = NSTAGE_FIT > 8 ? 8 : NSTAGE_FIT;  // half tiles staged in shared memory
+    static constexpr int SMEM = A_BYTES + NSTAGE * (STAGE_BYTES + F_BYTES) + RING_BYTES;
+    // and at least enough that no third CTA fits beside them (two CTAs take all 512 TMEM columns)
+    static constexpr int SMEM_REQ = SMEM > 80 * 1024 ? SMEM : 80 * 1024;
+    static_assert(NSTAGE >= 2, "shared memory stages");
 };
 
 // Byte offset of (row r, column k) in a no-swizzle K-major tile with KT columns.
