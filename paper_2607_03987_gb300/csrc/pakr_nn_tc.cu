@@ -284,31 +284,43 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
             const uint32_t done0 = smem_u32(&s_done[0]), empty0 = smem_u32(&s_empty[0]);
             uint32_t st8 = 0, fpar = 0;  // stage * 8 (mbarrier byte offset), its phase parity
             uint64_t bd = bdesc;
-            for (int t = 0; t < ntiles; ++t) {
-                const uint32_t ac = (uint32_t)t & 1u;
-                // the stage is masked, and the accumulator it will use (tile t - 2's) has been read
-                if (!mbar_wait_bounded(full0 + st8, fpar, kWaitNs) ||
-                    (t >= kTcAcc && !mbar_wait_bounded(empty0 + 8 * ac, (((uint32_t)t >> 1) + 1u) & 1u, kWaitNs))) {
-                    s_abort = 1;
-                    atomicOr(&ctl->err, ERR_TC_TIMEOUT);
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t dt = tbase + ac * (uint32_t)kTcBN;
-                mma_tf32_ss_c<false>(dt, adesc, bd, idesc);
+            uint32_t epar = 0;  // phase parity of the accumulators' release barriers
+            // two tiles per trip, one per accumulator, so that the accumulator is a constant
+            for (int t = 0; t < ntiles; t += kTcAcc) {
+                bool live = true;
 #pragma unroll
-                for (int s = 1; s < KT / 8; ++s)
-                    mma_tf32_ss_c<true>(dt, adesc + (uint64_t)((2 * S::LBO * s) >> 4),
-                                        bd + (uint64_t)((2 * S::LBO * s) >> 4), idesc);
-                mma_commit(free0 + st8);
-                mma_commit(done0 + 8 * ac);
-                st8 += 8;
-                bd += (uint64_t)(S::STAGE_BYTES >> 4);
-                if (st8 == 8 * NST) {
-                    st8 = 0;
-                    fpar ^= 1u;
-                    bd = bdesc;
+                for (int ac = 0; ac < kTcAcc; ++ac) {
+                    if (!live || t + ac >= ntiles)
+                        break;
+                    // the accumulator has been read (tile t + ac - 2's; usually the longer wait,
+                    // so it comes first), and the stage is masked
+                    if ((t > 0 && !mbar_wait_bounded(empty0 + 8 * ac, epar ^ 1u, kWaitNs)) ||
+                        !mbar_wait_bounded(full0 + st8, fpar, kWaitNs)) {
+                        s_abort = 1;
+                        atomicOr(&ctl->err, ERR_TC_TIMEOUT);
+                        live = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dt = tbase + (uint32_t)(ac * kTcBN);
+                    mma_tf32_ss_c<false>(dt, adesc, bd, idesc);
+#pragma unroll
+                    for (int s = 1; s < KT / 8; ++s)
+                        mma_tf32_ss_c<true>(dt, adesc + (uint64_t)((2 * S::LBO * s) >> 4),
+                                            bd + (uint64_t)((2 * S::LBO * s) >> 4), idesc);
+                    mma_commit(free0 + st8);
+                    mma_commit(done0 + 8 * ac);
+                    st8 += 8;
+                    bd += (uint64_t)(S::STAGE_BYTES >> 4);
+                    if (st8 == 8 * NST) {
+                        st8 = 0;
+                        fpar ^= 1u;
+                        bd = bdesc;
+                    }
                 }
+                if (!live)
+                    break;
+                epar ^= 1u;
             }
         }
         __syncwarp();
