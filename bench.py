@@ -127,9 +127,9 @@ def measured_peaks():
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one tensor-core nearest-neighbour launch
 # (k_nn_tc) on the bench workload (n = 1,000,000 nodes, d = 6) from one ncu capture of the
-# current kernel (read 127.03 MB: the 96 MB packed operand copy, f-costs and the exact
-# resolve's coordinate rows; written 3.78 MB).
-NN_DRAM_BYTES_NCU = 127.03e6 + 3.78e6
+# current kernel (read 109.77 MB: the 96 MB packed operand copy, f-costs and the packed rows
+# of the exact resolve's candidate groups; written 3.71 MB).
+NN_DRAM_BYTES_NCU = 109.77e6 + 3.71e6
 
 # Nominal dense TF32 / BF16 tensor throughput ratio (1.1 / 2.25 PFLOP/s): the TF32 peak is
 # the measured BF16 GEMM rate times this.
@@ -161,7 +161,7 @@ def nn_uses_tensor_cores(spec, n):
     mode = spec.get("nn_mode", 0)
     if mode == 2:
         return True
-    return mode == 0 and spec["K"] >= 256 and n >= 65536
+    return mode == 0 and spec["K"] >= 256 and n >= 40960
 
 
 def nn_bytes_per_launch(n, d):

@@ -198,9 +198,10 @@ pakr_status check_desc(const pakr_problem_desc *d, DimInfo *di)
 }
 
 // Smallest tree size the tensor-core nearest neighbour takes (0x7FFFFFFF: never), and
-// the floats per packed node row it needs (0: no packed copy).  Below about 64k nodes, or
-// with fewer than two query blocks, the FP32 kernel is faster.
-constexpr int kTcAutoMinNodes = 65536;
+// the floats per packed node row it needs (0: no packed copy).  Below about 40k nodes, or
+// with fewer than two query blocks, the FP32 kernel is faster (d = 6, 1024 queries: equal
+// at 32k nodes, 30.7 vs 34.9 us at 48k).
+constexpr int kTcAutoMinNodes = 40960;
 constexpr int kTcAutoMinQueries = 256;
 int tc_min_nodes(const pakr_problem_desc *d)
 {

@@ -125,7 +125,8 @@ def test_expand_graph_matches_plain_launches(cuda_lib):
     # without profiling pakr_expand launches one graph (IF nodes pick the kernel); with
     # profiling it launches the kernels one by one: same tree, bounds and seeds, same results
     spec = W.with_sizes(W.problem("di3", env_seed=9), K=512, k=4, cap=200_000)
-    tree = W.prefilled_tree(spec, 60_000, seed=17, cost_hi=2.0)
+    n0 = 39_000  # just below the automatic switch to the tensor-core kernel (40960 nodes)
+    tree = W.prefilled_tree(spec, n0, seed=17, cost_hi=2.0)
     out = []
     for profile in (False, True):
         planner = pakr.Planner(spec)
@@ -133,7 +134,7 @@ def test_expand_graph_matches_plain_launches(cuda_lib):
             planner.tree_import(tree, spec["x_goal"])
             planner.set_profiling(profile)
             recs = []
-            for bound, seed in ((np.inf, 1), (1.8, 2), (np.inf, 3), (1.2, 4)):  # the tree crosses 65536 nodes
+            for bound, seed in ((np.inf, 1), (1.8, 2), (np.inf, 3), (1.2, 4)):  # the tree crosses the switch
                 st, info = planner.expand(bound, seed)
                 recs.append((st, info, planner.debug_last_expand()))
             out.append((recs, planner.tree_size()))
@@ -141,6 +142,7 @@ def test_expand_graph_matches_plain_launches(cuda_lib):
             planner.close()
     (ra, na), (rb, nb) = out
     assert na == nb
+    assert na > 40960, "the expansions must cross into the tensor-core kernel's range"
     for (sa, ia, da), (sb, ib, db) in zip(ra, rb):
         assert sa == sb and ia == ib
         for key in ("samples", "near", "outcome", "controls", "steps"):
