@@ -73,7 +73,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Byte offsets of every device buffer inside one allocation.
 struct Layout {
     size_t X, U, cost, fcost, parent, steps, XT;
-    size_t xr, nn_key, st_x, st_u, st_cost, st_f, st_steps, st_parent, outcome, goal, block_count;
+    size_t xr, nn_key, nn_amin, st_x, st_u, st_cost, st_f, st_steps, st_parent, outcome, goal, block_count;
     size_t boxes, spheres, ctl, pp;
     size_t path_nodes, path_x, path_u, path_steps, hist_t, hist_cost, hist_iter;
     size_t total;
@@ -102,6 +102,7 @@ Layout make_layout(const DimInfo &di, int64_t cap, int K, int k, int nb, int ns,
     L.XT = take(tc_row_floats > 0 ? sizeof(float) * (size_t)tc_row_floats * ((c + 255) / 256 * 256) : 0);
     L.xr = take(sizeof(float) * di.d * (size_t)K);
     L.nn_key = take(sizeof(unsigned long long) * (size_t)K);
+    L.nn_amin = take(sizeof(unsigned) * (size_t)K);
     L.st_x = take(sizeof(float) * di.d * R);
     L.st_u = take(sizeof(float) * di.m * R);
     L.st_cost = take(sizeof(float) * R);
@@ -707,7 +708,7 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
                    (float *)(b + L.st_cost),  (float *)(b + L.st_f),
                    (int *)(b + L.st_steps),   (int *)(b + L.st_parent),
                    (int8_t *)(b + L.outcome), (int8_t *)(b + L.goal),
-                   (int *)(b + L.block_count)};
+                   (int *)(b + L.block_count), (unsigned *)(b + L.nn_amin)};
     p->ctl = (Ctl *)(b + L.ctl);
     p->pp = (PlanParams *)(b + L.pp);
     p->B = DevPlanBufs{(int *)(b + L.path_nodes), (float *)(b + L.path_x), (float *)(b + L.path_u),

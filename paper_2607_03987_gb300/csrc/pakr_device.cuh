@@ -285,6 +285,8 @@ __device__ __forceinline__ void sample_state(const DevProblem &P, const DevWork 
         }
     }
     W.nn_key[i] = kNoKey;
+    if (W.nn_amin)
+        W.nn_amin[i] = 0xFFFFFFFFu;
 }
 
 // Per-batch reset of a control block: the bound, the frozen tree size and the counters.

@@ -67,6 +67,8 @@ struct DevWork {
     int8_t *outcome;            // R
     int8_t *goal;               // R
     int *block_count;           // one per propagate block
+    unsigned *nn_amin = nullptr;  // K: smallest tensor-core filter value per query over node chunks
+                                  // (order-preserving unsigned encoding; all ones = none yet)
 };
 
 // Device control block: tree counter, per-batch scalars and AO-x state.

@@ -112,6 +112,18 @@ __device__ __forceinline__ void tc_prefetch_group(const DevTree &T, int g0)
     asm volatile("prefetch.global.L2 [%0];" ::"l"(T.fcost + g0));
 }
 
+// Order-preserving map of a float onto unsigned (smaller float, smaller key), so that the
+// per-query filter minimum over node chunks can use the integer atomicMin.
+__device__ __forceinline__ unsigned tc_ord(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float tc_unord(unsigned k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
 // grid (chunks, ceil(K / 128)), kTcThreads threads, TcShape<D>::SMEM_REQ dynamic shared memory;
 // two CTAs per SM.  T.fcost must be readable 4 floats past the node count (the f-cost copy
 // rounds up to 16 bytes).
@@ -334,6 +346,12 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
         const float Rq = sqrtf(qc2) * 1.0001f + sqrtf(P.tc_xbox2);
         band = 2.f * tc_bound_coef<D>() * Rq * Rq;
         float thr = kTcEligible;
+        // The filter value a differs from the distance by a per-query constant, so minima from
+        // other node chunks prune this chunk's candidates too: every 32 tiles the running
+        // minimum is published (a fire-and-forget atomicMin) and the shared one is read back,
+        // to be used one period later so that the load never stalls the loop.
+        const bool pub = W.nn_amin != nullptr && qid < K;
+        unsigned gkey = 0xFFFFFFFFu;
         for (int t = 0; t < ntiles; ++t) {
             const int b = t % kTcAcc;
             const bool ok =
@@ -370,6 +388,14 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
                 for (int h4 = 0; h4 < 4; ++h4)
                     m[4 + h4] = min16(v + 16 * h4);
             }
+            if ((t & 31) == 31 && pub) {
+                const float g = tc_unord(gkey);  // the value read one period ago
+                if (g < m1)
+                    thr = fminf(thr, g + band);
+                if (m1 < kTcEligible)
+                    atomicMin(W.nn_amin + qid, tc_ord(m1));
+                gkey = __ldcg(W.nn_amin + qid);
+            }
             const float mm = fminf(fmin3(m[0], m[1], m[2]), fmin3(m[3], fmin3(m[4], m[5], m[6]), m[7]));
             if (mm <= thr) {
 #pragma unroll
@@ -377,7 +403,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
                     if (m[h8] <= thr) {
                         if (m[h8] < m1) {
                             m1 = m[h8];
-                            thr = m1 + band;
+                            thr = fminf(thr, m1 + band);
                         }
                         const int slot = pos & (kTcRing - 1);
                         // an entry still within the band would be lost: the row falls back to a rescan
@@ -390,6 +416,8 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
                 }
             }
         }
+        if (pub && m1 < kTcEligible)
+            atomicMin(W.nn_amin + qid, tc_ord(m1));
     }
     tc_fence_before();
     __syncthreads();
@@ -402,7 +430,9 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
 
     // ---- exact resolve of the candidate groups ----
     if (!flagged && warp >= kTcReader0 && qid < K && m1 < kTcEligible) {
-        const float thrf = m1 + band;
+        // against the smallest filter value any chunk has published by now (this chunk's
+        // included): groups above it by more than the band cannot hold the nearest node
+        const float thrf = (W.nn_amin ? fminf(m1, tc_unord(__ldcg(W.nn_amin + qid))) : m1) + band;
         if (!ovf) {
             // every CTA resolves at the same moment, and the streamed tiles have mostly left
             // L2 by now: request all surviving groups' lines first, so that their DRAM round
