@@ -62,33 +62,38 @@ __device__ __forceinline__ void tc_resolve_group(const DevTree &T, int g0, int e
 {
     using S = TcShape<D>;
     constexpr int NC = (2 * D + 3) / 4;  // 16-byte chunks holding x_hi and x_lo of a row
+    constexpr int RB = 4;                // rows per batch of loads
     const unsigned char *tile = reinterpret_cast<const unsigned char *>(T.XT) + (size_t)(g0 / kTcN) * S::TILE_BYTES;
     const int r0 = g0 % kTcN;
 #pragma unroll 1
     for (int q4 = 0; q4 < kTcG; q4 += 4) {
-        float4 ch[4][NC];
-#pragma unroll
-        for (int g = 0; g < 4; ++g)
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-                ch[g][c] = *reinterpret_cast<const float4 *>(tile + tc_off<D>(r0 + q4 + g, 4 * c));
         const float4 f4 = *reinterpret_cast<const float4 *>(T.fcost + g0 + q4);
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            const float *row = reinterpret_cast<const float *>(ch[g]);
-            float acc = 0.f;
+        for (int g2 = 0; g2 < 4; g2 += RB) {
+            float4 ch[RB][NC];
 #pragma unroll
-            for (int a = 0; a < D; ++a) {
-                const float xc = __fadd_rn(row[a], row[D + a]);
-                const float diff = __fadd_rn(qv[a], -xc);
-                acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
-            }
-            const float f = g == 0 ? f4.x : g == 1 ? f4.y : g == 2 ? f4.z : f4.w;
-            const int j = g0 + q4 + g;
-            const float ex = (f < bound) ? acc : __int_as_float(0x7f800000);
-            if (j < end && (ex < best || (ex == best && j < bidx))) {
-                best = ex;
-                bidx = j;
+            for (int g = 0; g < RB; ++g)
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    ch[g][c] = *reinterpret_cast<const float4 *>(tile + tc_off<D>(r0 + q4 + g2 + g, 4 * c));
+#pragma unroll
+            for (int g = 0; g < RB; ++g) {
+                const float *row = reinterpret_cast<const float *>(ch[g]);
+                float acc = 0.f;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const float xc = __fadd_rn(row[a], row[D + a]);
+                    const float diff = __fadd_rn(qv[a], -xc);
+                    acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
+                }
+                const int gg = g2 + g;
+                const float f = gg == 0 ? f4.x : gg == 1 ? f4.y : gg == 2 ? f4.z : f4.w;
+                const int j = g0 + q4 + gg;
+                const float ex = (f < bound) ? acc : __int_as_float(0x7f800000);
+                if (j < end && (ex < best || (ex == best && j < bidx))) {
+                    best = ex;
+                    bidx = j;
+                }
             }
         }
     }
@@ -124,11 +129,11 @@ __device__ __forceinline__ float tc_unord(unsigned k)
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
-// grid (chunks, ceil(K / 128)), kTcThreads threads, TcShape<D>::SMEM_REQ dynamic shared memory;
+// grid (chunks, ceil(K / 128)), TcShape<D>::THREADS threads, TcShape<D>::SMEM_REQ dynamic shared memory;
 // two CTAs per SM.  T.fcost must be readable 4 floats past the node count (the f-cost copy
 // rounds up to 16 bytes).
 template <int D>
-__global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
+__global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
     k_nn_tc(DevProblem P, Ctl *__restrict__ ctl, DevTree T, DevWork W)
 {
     using S = TcShape<D>;
@@ -139,12 +144,12 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
     unsigned char *sB0 = tc_smem + S::A_BYTES;
     float *sF0 = reinterpret_cast<float *>(tc_smem + S::A_BYTES + NST * S::STAGE_BYTES);
     float *ring_val = reinterpret_cast<float *>(tc_smem + S::A_BYTES + NST * (S::STAGE_BYTES + S::F_BYTES));
-    int *ring_grp = reinterpret_cast<int *>(ring_val + kTcRing * kTcReaders);
+    int *ring_grp = reinterpret_cast<int *>(ring_val + kTcRing * S::READERS);
     __shared__ __align__(8) unsigned long long s_loaded[NST], s_full[NST], s_free[NST];
     __shared__ __align__(8) unsigned long long s_done[kTcAcc], s_empty[kTcAcc];
     __shared__ uint32_t s_tbase;
     __shared__ volatile int s_abort;
-    __shared__ int s_nflag, s_flag_qid[kTcM];
+    __shared__ int s_nflag, s_flag_qid[kTcM], s_ovf[kTcM];
     __shared__ float s_flag_q[kTcM][D];
 
     const int n = ctl->n_start;
@@ -181,13 +186,14 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
 #pragma unroll
         for (int i = 0; i < kTcAcc; ++i) {
             mbar_init(smem_u32(&s_done[i]), 1);
-            mbar_init(smem_u32(&s_empty[i]), kTcReaders / 32);
+            mbar_init(smem_u32(&s_empty[i]), S::READERS / 32);
         }
         fence_mbar_init();
         s_abort = 0;
         s_nflag = 0;
     }
     if (tid < kTcM) {
+        s_ovf[tid] = 0;
         // query row: -2 (q - c) split as hi (against x_hi), hi (against x_lo), lo (against x_hi); 1, 1
         const int q = qbase + tid;
         float row[KT];
@@ -217,10 +223,10 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
     tc_fence_after();
     const uint32_t tbase = s_tbase;
 
-    // reader state: one reader thread per query row
-    const int quarter = warp & 3;
+    // reader state: two reader threads per query row, one per 64-column half of the accumulator
+    const int quarter = warp & 3, half = (warp - kTcReader0) >> 2;
     const int qrow = 32 * quarter + lane;
-    const int e = qrow;  // ring column
+    const int e = tid - kTcReader0 * 32;  // ring column
     const int qid = qbase + qrow;
     float qv[D];
     float m1 = kTcEligible;
@@ -364,14 +370,30 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
                 break;
             }
             tc_fence_after();
-            const uint32_t tcol = tbase + (uint32_t)(b * kTcBN) + ((uint32_t)(32 * quarter) << 16);
-            const int gbase = start + t * kTcBN;
-            // minima of this row's eight 16-node groups: two 64-column loads, the accumulator is
-            // released after the second; one branch per tile (the candidate test rarely passes
+            constexpr int CW = kTcBN / S::RH;  // accumulator columns of this reader
+            constexpr int NG = CW / kTcG;      // 16-node groups it reduces per tile
+            const uint32_t tcol = tbase + (uint32_t)(b * kTcBN + CW * half) + ((uint32_t)(32 * quarter) << 16);
+            const int gbase = start + t * kTcBN + CW * half;
+            // minima of this reader's 16-node groups: two loads of CW / 2 columns, the accumulator
+            // is released after the second; one branch per tile (the candidate test rarely passes
             // once the running minimum has settled, and a branch per group would stall the warp
             // on every minimum tree)
-            float m[8];
-            {
+            float m[NG];
+            if constexpr (S::RH == 2) {
+                float v[32];
+                __syncwarp();
+                tmem_ld32(tcol, v);
+                m[0] = min16(v);
+                m[1] = min16(v + 16);
+                __syncwarp();
+                tmem_ld32(tcol + 32, v);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(smem_u32(&s_empty[b]));
+                m[2] = min16(v);
+                m[3] = min16(v + 16);
+            } else {
                 float v[64];
                 __syncwarp();
                 tmem_ld64(tcol, v);
@@ -396,10 +418,13 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
                     atomicMin(W.nn_amin + qid, tc_ord(m1));
                 gkey = __ldcg(W.nn_amin + qid);
             }
-            const float mm = fminf(fmin3(m[0], m[1], m[2]), fmin3(m[3], fmin3(m[4], m[5], m[6]), m[7]));
+            float mm = m[0];
+#pragma unroll
+            for (int h = 1; h < NG; ++h)
+                mm = fminf(mm, m[h]);
             if (mm <= thr) {
 #pragma unroll
-                for (int h8 = 0; h8 < 8; ++h8) {
+                for (int h8 = 0; h8 < NG; ++h8) {
                     if (m[h8] <= thr) {
                         if (m[h8] < m1) {
                             m1 = m[h8];
@@ -407,10 +432,10 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
                         }
                         const int slot = pos & (kTcRing - 1);
                         // an entry still within the band would be lost: the row falls back to a rescan
-                        if (pos >= kTcRing && ring_val[slot * kTcReaders + e] <= thr)
+                        if (pos >= kTcRing && ring_val[slot * S::READERS + e] <= thr)
                             ovf = 1;
-                        ring_val[slot * kTcReaders + e] = m[h8];
-                        ring_grp[slot * kTcReaders + e] = gbase + 16 * h8;
+                        ring_val[slot * S::READERS + e] = m[h8];
+                        ring_grp[slot * S::READERS + e] = gbase + 16 * h8;
                         ++pos;
                     }
                 }
@@ -418,6 +443,8 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
         }
         if (pub && m1 < kTcEligible)
             atomicMin(W.nn_amin + qid, tc_ord(m1));
+        if (ovf)
+            s_ovf[qrow] = 1;
     }
     tc_fence_before();
     __syncthreads();
@@ -429,31 +456,32 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
         return;
 
     // ---- exact resolve of the candidate groups ----
-    if (!flagged && warp >= kTcReader0 && qid < K && m1 < kTcEligible) {
+    if (!flagged && warp >= kTcReader0 && qid < K && (m1 < kTcEligible || s_ovf[qrow])) {
         // against the smallest filter value any chunk has published by now (this chunk's
         // included): groups above it by more than the band cannot hold the nearest node
         const float thrf = (W.nn_amin ? fminf(m1, tc_unord(__ldcg(W.nn_amin + qid))) : m1) + band;
-        if (!ovf) {
+        // a row either of whose readers lost a candidate is rescanned instead (once)
+        if (!s_ovf[qrow]) {
             // every CTA resolves at the same moment, and the streamed tiles have mostly left
             // L2 by now: request all surviving groups' lines first, so that their DRAM round
             // trips overlap instead of following one another group by group
             const int np = min(pos, kTcRing);
 #pragma unroll 1
             for (int s = 0; s < np; ++s)
-                if (ring_val[s * kTcReaders + e] <= thrf)
-                    tc_prefetch_group<D>(T, ring_grp[s * kTcReaders + e]);
+                if (ring_val[s * S::READERS + e] <= thrf)
+                    tc_prefetch_group<D>(T, ring_grp[s * S::READERS + e]);
             float best = __int_as_float(0x7f800000);
             int bidx = 0x7FFFFFFF;
 #pragma unroll 1
             for (int s = 0; s < np; ++s) {
-                if (!(ring_val[s * kTcReaders + e] <= thrf))
+                if (!(ring_val[s * S::READERS + e] <= thrf))
                     continue;
-                tc_resolve_group<D>(T, ring_grp[s * kTcReaders + e], end, bound, qv, best, bidx);
+                tc_resolve_group<D>(T, ring_grp[s * S::READERS + e], end, bound, qv, best, bidx);
             }
             if (best < __int_as_float(0x7f800000))
                 atomicMin(&W.nn_key[qid],
                           ((unsigned long long)__float_as_uint(best) << 32) | (unsigned long long)(uint32_t)bidx);
-        } else {
+        } else if (half == 0) {
             const int slot = atomicAdd(&s_nflag, 1);
             s_flag_qid[slot] = qid;
 #pragma unroll
@@ -481,7 +509,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
         for (int a = 0; a < D; ++a)
             q2[a] = s_flag_q[f][a];
         unsigned long long key = kNoKey;
-        for (int j = start + tid; j < end; j += kTcThreads) {
+        for (int j = start + tid; j < end; j += S::THREADS) {
             const float ed = tc_exact<D>(P, T, j, bound, q2);
             if (ed < __int_as_float(0x7f800000)) {
                 const unsigned long long k2 =
@@ -516,7 +544,7 @@ template <int D>
 static cudaError_t launch_nn_tc_d(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W,
                                   const LaunchCfg &L, cudaStream_t s)
 {
-    k_nn_tc<D><<<dim3(L.tc_chunks, L.tc_qblocks), kTcThreads, TcShape<D>::SMEM_REQ, s>>>(P, ctl, T, W);
+    k_nn_tc<D><<<dim3(L.tc_chunks, L.tc_qblocks), TcShape<D>::THREADS, TcShape<D>::SMEM_REQ, s>>>(P, ctl, T, W);
     return cudaGetLastError();
 }
 

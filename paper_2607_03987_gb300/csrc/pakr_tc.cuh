@@ -187,6 +187,25 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64])
     for (int i = 0; i < 64; ++i)
         v[i] = __uint_as_float(r[i]);
 }
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane, loaded and waited for.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ float fmin3(float a, float b, float c)
 {
     float r;
@@ -225,7 +244,6 @@ constexpr int kTcN = 256;        // nodes per tile of the packed operand copy
 constexpr int kTcBN = 128;       // nodes per pipeline stage and MMA (N): half a packed tile
 constexpr int kTcAcc = 2;        // accumulators of kTcBN columns per CTA
 constexpr int kTcCols = kTcAcc * kTcBN;  // TMEM columns per CTA: two CTAs share an SM's 512
-constexpr int kTcReaders = 128;  // 4 accumulator-reader warps, one per TMEM lane quarter
 constexpr int kTcG = 16;         // nodes per filter group
 constexpr int kTcRing = 8;       // candidate groups remembered per (query, reader)
 constexpr float kTcSentinel = 1.2676506e30f;  // 2^100: |x - c|^2 of ineligible and padding nodes
@@ -234,8 +252,7 @@ constexpr float kTcEligible = 6.338253e29f;   // 2^99: filter values at or above
 constexpr int kTcLoadWarp = 0;   // lane 0: bulk copies of node half tiles and f-costs
 constexpr int kTcMmaWarp = 1;    // lane 0: MMAs; the warp owns the TMEM allocation
 constexpr int kTcPatch0 = 2;     // warps 2-3: mask ineligible rows, signal "stage masked"
-constexpr int kTcReader0 = 4;    // warps 4-7: accumulator readers (warp w reads lane quarter w % 4)
-constexpr int kTcThreads = kTcReader0 * 32 + kTcReaders;
+constexpr int kTcReader0 = 4;    // warps 4 and up: accumulator readers (warp w reads lane quarter w % 4)
 
 template <int D>
 struct TcShape {
@@ -245,7 +262,13 @@ struct TcShape {
     static constexpr int STAGE_BYTES = kTcBN * KT * 4;     // half a packed tile: also contiguous
     static constexpr int A_BYTES = kTcM * KT * 4;
     static constexpr int F_BYTES = kTcBN * 4;
-    static constexpr int RING_BYTES = kTcRing * kTcReaders * 8;
+    // reader warps per TMEM lane quarter: two (64 accumulator columns each) for d <= 8, one
+    // (all 128) for larger d, whose resolve needs the registers (measured both ways: d = 6
+    // gains 3 %, d = 12 loses 3-6 % with two)
+    static constexpr int RH = D <= 8 ? 2 : 1;
+    static constexpr int READERS = 128 * RH;
+    static constexpr int THREADS = kTcReader0 * 32 + READERS;
+    static constexpr int RING_BYTES = kTcRing * READERS * 8;
     // two CTAs per SM: each within half of the SM's 228 KB, static shared memory included
     static constexpr int NSTAGE_FIT = (100 * 1024 - A_BYTES - RING_BYTES) / (STAGE_BYTES + F_BYTES);
     static constexpr int NSTAGE = NSTAGE_FIT > 8 ? 8 : NSTAGE_FIT;  // half tiles staged in shared memory
