@@ -127,9 +127,9 @@ def measured_peaks():
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one tensor-core nearest-neighbour launch
 # (k_nn_tc) on the bench workload (n = 1,000,000 nodes, d = 6) from one ncu capture of the
-# current kernel (read 109.77 MB: the 96 MB packed operand copy, f-costs and the packed rows
-# of the exact resolve's candidate groups; written 3.71 MB).
-NN_DRAM_BYTES_NCU = 109.77e6 + 3.71e6
+# current kernel (read 100.53 MB: the 96 MB packed operand copy, f-costs and the packed rows
+# of the exact resolve's candidate groups; written 3.48 MB).
+NN_DRAM_BYTES_NCU = 100.53e6 + 3.48e6
 
 # Nominal dense TF32 / BF16 tensor throughput ratio (1.1 / 2.25 PFLOP/s): the TF32 peak is
 # the measured BF16 GEMM rate times this.
