@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(NT, (NnMinBlocks<Dims<DYN>::D, NT>::value))
             const BatchQueryDev &qd = Q[q];
             if (qd.ctl->plan_stop)
                 continue;
-            append_block<D, M>(qd.P, qd.ctl, qd.T, qd.W, vb, nblk, NT, s_tmp, s_warp);
+            append_block<D, M>(qd.P, qd.ctl, qd.T, qd.W, vb, nblk, NT, 1, s_tmp, s_warp);
         }
         grid.sync();
 

@@ -815,27 +815,57 @@ __device__ __forceinline__ int block_sum(int v, int *s_tmp)
     return tot;
 }
 
-// Append the survivors of propagate block vb; rpb rollouts per block are
-// handled by the first rpb threads (the rest take part in the scans only).
+// Append the survivors of propagate blocks vb * pbs .. vb * pbs + pbs - 1 (rpb rollouts each),
+// handled by the first rpb * pbs threads (the rest take part in the scans only).  blockDim.x is a
+// multiple of 32: the scans are warp-wide.
 template <int D, int M>
 __device__ __forceinline__ void append_block(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, int vb,
-                                             int nblk, int rpb, int *s_tmp, int *s_warp)
+                                             int nblk, int rpb, int pbs, int *s_tmp, int *s_warp)
 {
     const int R = P.K * P.k;
+    const int rpa = rpb * pbs;
+    const int r = vb * rpa + threadIdx.x;
+    const bool cand = ((int)threadIdx.x < rpa) && (r < R) && (W.outcome[r] == OUT_APPENDED);
+    // the candidate's staged child is loaded before the prefix below, so that both round trips
+    // to memory overlap
+    float xs[D], us[M];
+    float c = 0.f, fv = 0.f;
+    int parent = 0, steps = 0;
+    bool goal = false;
+    if (cand) {
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            xs[a] = W.st_x[(size_t)a * R + r];
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+            us[a] = W.st_u[(size_t)a * R + r];
+        c = W.st_cost[r];
+        fv = W.st_f[r];
+        parent = W.st_parent[r];
+        steps = W.st_steps[r];
+        goal = W.goal[r] != 0;
+    }
+    // survivors of the blocks before this one, and of all: eight independent loads in flight
     int part = 0, tot = 0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-        const int c = W.block_count[b];
-        tot += c;
-        if (b < vb)
-            part += c;
+    for (int b0 = threadIdx.x; b0 < nblk; b0 += 8 * (int)blockDim.x) {
+        int cnt[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int b = b0 + u * (int)blockDim.x;
+            cnt[u] = b < nblk ? W.block_count[b] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            tot += cnt[u];
+            if (b0 + u * (int)blockDim.x < vb * pbs)
+                part += cnt[u];
+        }
     }
     part = block_sum(part, s_tmp);
     tot = block_sum(tot, s_tmp);
 
     const int n_start = ctl->n_start;
     const int cap = P.cap;
-    const int r = vb * rpb + threadIdx.x;
-    const bool cand = ((int)threadIdx.x < rpb) && (r < R) && (W.outcome[r] == OUT_APPENDED);
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, cand);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0)
@@ -848,22 +878,18 @@ __device__ __forceinline__ void append_block(const DevProblem &P, Ctl *ctl, cons
     if (cand) {
         if (pos < cap) {
             const int p = (int)pos;
-            float xs[D];
 #pragma unroll
-            for (int a = 0; a < D; ++a) {
-                xs[a] = W.st_x[(size_t)a * R + r];
+            for (int a = 0; a < D; ++a)
                 T.X[(size_t)a * cap + p] = xs[a];
-            }
             tc_pack_node<D>(P, T, ctl, p, xs);
 #pragma unroll
             for (int a = 0; a < M; ++a)
-                T.U[(size_t)a * cap + p] = W.st_u[(size_t)a * R + r];
-            const float c = W.st_cost[r];
+                T.U[(size_t)a * cap + p] = us[a];
             T.cost[p] = c;
-            T.fcost[p] = W.st_f[r];
-            T.parent[p] = W.st_parent[r];
-            T.steps[p] = W.st_steps[r];
-            if (W.goal[r])
+            T.fcost[p] = fv;
+            T.parent[p] = parent;
+            T.steps[p] = steps;
+            if (goal)
                 atomicMin(&ctl->goal_key, ((unsigned long long)__float_as_uint(c) << 32) | (unsigned long long)p);
         } else {
             W.outcome[r] = OUT_DROPPED;

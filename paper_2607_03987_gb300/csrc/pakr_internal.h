@@ -20,6 +20,7 @@ enum { H_POSITION = 0, H_FULLSTATE = 1 };
 enum { MODE_EXPAND = 0, MODE_PLAN = 1 };
 enum { ERR_PATH_CYCLE = 1, ERR_BAD_PARENT = 2, ERR_TC_TIMEOUT = 4 };
 constexpr int kTcCtasPerSm = 2;  // resident tensor-core nearest-neighbour CTAs per SM
+constexpr int kMaxPropLanes = 16;  // lanes per rollout in k_propagate at most
 
 // Problem constants, passed to every kernel by value.
 struct DevProblem {
@@ -126,7 +127,7 @@ struct LaunchCfg {
     int nn_variant;     // 0: 64 threads x 2 queries, 1: 128 x 2, 2: 256 x 4
     int nn_threads, nn_qpt, nn_qgroups, nn_chunks;
     int prop_threads, prop_blocks;
-    int prop_lanes;     // lanes per rollout in k_propagate (1, 2, 4 or 8); k_append takes prop_threads / prop_lanes
+    int prop_lanes;     // lanes per rollout in k_propagate (1, 2, 4, 8 or 16, at most kMaxPropLanes)
     int sample_threads, sample_blocks;
     int obs_smem_bytes; // shared memory for obstacles + goal
     int tc_chunks, tc_qblocks;  // tensor-core nearest neighbour grid (node chunks x query blocks)

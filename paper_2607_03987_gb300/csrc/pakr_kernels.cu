@@ -67,11 +67,11 @@ __global__ void __launch_bounds__(256) k_propagate(DevProblem P, Ctl *ctl, DevTr
 }
 
 template <int D, int M>
-__global__ void __launch_bounds__(256) k_append(DevProblem P, Ctl *ctl, DevTree T, DevWork W, int nblk)
+__global__ void __launch_bounds__(256) k_append(DevProblem P, Ctl *ctl, DevTree T, DevWork W, int nblk, int rpb)
 {
     __shared__ int s_tmp[32];
     __shared__ int s_warp[32];
-    append_block<D, M>(P, ctl, T, W, blockIdx.x, nblk, blockDim.x, s_tmp, s_warp);
+    append_block<D, M>(P, ctl, T, W, blockIdx.x, nblk, rpb, (int)blockDim.x / rpb, s_tmp, s_warp);
 }
 
 // ---------------------------------------------------------------------------
@@ -250,6 +250,7 @@ static cudaError_t launch_propagate_dyn(const DevProblem &P, Ctl *ctl, const Dev
     case 2: k_propagate<DYN, 2><<<L.prop_blocks, L.prop_threads, L.obs_smem_bytes, s>>>(P, ctl, T, W); break;
     case 4: k_propagate<DYN, 4><<<L.prop_blocks, L.prop_threads, L.obs_smem_bytes, s>>>(P, ctl, T, W); break;
     case 8: k_propagate<DYN, 8><<<L.prop_blocks, L.prop_threads, L.obs_smem_bytes, s>>>(P, ctl, T, W); break;
+    case 16: k_propagate<DYN, 16><<<L.prop_blocks, L.prop_threads, L.obs_smem_bytes, s>>>(P, ctl, T, W); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -265,9 +266,13 @@ cudaError_t launch_propagate(const DevProblem &P, Ctl *ctl, const DevTree &T, co
 cudaError_t launch_append(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
                           cudaStream_t s)
 {
+    // one thread per rollout, at least a warp per block (the scans are warp-wide): with more
+    // than 8 lanes per rollout an append block covers several propagate blocks
     const int rollouts_per_block = L.prop_threads / L.prop_lanes;
-    PAKR_DISPATCH_DYN(P.dyn, (k_append<Dims<DYN_>::D, Dims<DYN_>::M><<<L.prop_blocks, rollouts_per_block, 0, s>>>(
-                                 P, ctl, T, W, L.prop_blocks)));
+    const int threads = rollouts_per_block < 32 ? 32 : rollouts_per_block;
+    const int pbs = threads / rollouts_per_block;
+    PAKR_DISPATCH_DYN(P.dyn, (k_append<Dims<DYN_>::D, Dims<DYN_>::M><<<(L.prop_blocks + pbs - 1) / pbs, threads, 0, s>>>(
+                                 P, ctl, T, W, L.prop_blocks, rollouts_per_block)));
     return cudaGetLastError();
 }
 
