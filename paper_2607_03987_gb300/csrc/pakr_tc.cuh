@@ -114,17 +114,8 @@ __device__ __forceinline__ bool mbar_wait_suspend(uint32_t bar, uint32_t parity,
             return false;
     }
 }
-// D[tmem] (+)= A[smem] * B[smem]^T, kind::tf32, one CTA.
-__device__ __forceinline__ void mma_tf32_ss(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                            uint32_t accumulate)
-{
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "setp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-                 "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-                 : "memory");
-}
-// The same with the accumulate flag fixed at compile time (no predicate computed per MMA).
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::tf32, one CTA; the accumulate flag ACC is fixed at
+// compile time (no predicate computed per MMA).
 template <bool ACC>
 __device__ __forceinline__ void mma_tf32_ss_c(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc)
 {
