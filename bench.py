@@ -161,7 +161,7 @@ def nn_uses_tensor_cores(spec, n):
     mode = spec.get("nn_mode", 0)
     if mode == 2:
         return True
-    return mode == 0 and spec["K"] >= 256 and n >= 40960
+    return mode == 0 and spec["K"] >= 256 and n >= 28672
 
 
 def nn_bytes_per_launch(n, d):

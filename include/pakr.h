@@ -87,7 +87,7 @@ typedef enum pakr_heuristic {
  * argmin, lowest index on a tie).  The tensor-core kernel needs a packed
  * operand copy of the tree (4 * (3d + 2 rounded up to 8) bytes per node). */
 typedef enum pakr_nn_mode {
-    PAKR_NN_AUTO = 0,           /* tensor cores for trees of >= 40960 nodes when n_parents >= 256, FP32 otherwise */
+    PAKR_NN_AUTO = 0,           /* tensor cores for trees of >= 28672 nodes when n_parents >= 256, FP32 otherwise */
     PAKR_NN_FP32 = 1,           /* FP32 kernel only; no packed copy is kept */
     PAKR_NN_TENSOR = 2          /* tensor-core kernel at every tree size */
 } pakr_nn_mode;

@@ -199,10 +199,10 @@ pakr_status check_desc(const pakr_problem_desc *d, DimInfo *di)
 }
 
 // Smallest tree size the tensor-core nearest neighbour takes (0x7FFFFFFF: never), and
-// the floats per packed node row it needs (0: no packed copy).  Below about 40k nodes, or
-// with fewer than two query blocks, the FP32 kernel is faster (d = 6, 1024 queries: equal
-// at 32k nodes, 30.7 vs 34.9 us at 48k).
-constexpr int kTcAutoMinNodes = 40960;
+// the floats per packed node row it needs (0: no packed copy).  Below about 28k nodes, or
+// with fewer than two query blocks, the FP32 kernel in its 128-query blocks is faster
+// (d = 6, 1024 queries: 20.3 vs 25.1 us at 16k nodes, 30.8 vs 28.5 us at 32k).
+constexpr int kTcAutoMinNodes = 28672;
 constexpr int kTcAutoMinQueries = 256;
 int tc_min_nodes(const pakr_problem_desc *d)
 {
@@ -797,11 +797,16 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
     LaunchCfg &C = p->L;
     C.sample_threads = kSampleThreads;
     C.sample_blocks = (p->K + kSampleThreads - 1) / kSampleThreads;
-    if (p->K >= 1024) {
+    // With the tensor-core kernel on, the FP32 kernel only sees trees below its switch
+    // (28672 nodes): there, blocks of 1024 queries leave most SMs idle (a 4096-node tree fills
+    // 64 of 456 blocks), so the 128-query blocks are used instead (4096 nodes: 12.6 vs
+    // 16.4 us; 16384: 20.3 vs 25.3 us).
+    const bool nn_small_trees_only = tc_min_nodes(desc) < 0x7FFFFFFF;
+    if (p->K >= 1024 && !nn_small_trees_only) {
         C.nn_variant = 2;
         C.nn_threads = 256;
         C.nn_qpt = 4;
-    } else if (p->K >= 256) {
+    } else if (p->K >= 256 && !nn_small_trees_only) {
         C.nn_variant = 1;
         C.nn_threads = 128;
         C.nn_qpt = 2;

@@ -125,7 +125,7 @@ def test_expand_graph_matches_plain_launches(cuda_lib):
     # without profiling pakr_expand launches one graph (IF nodes pick the kernel); with
     # profiling it launches the kernels one by one: same tree, bounds and seeds, same results
     spec = W.with_sizes(W.problem("di3", env_seed=9), K=512, k=4, cap=200_000)
-    n0 = 40_800  # just below the automatic switch to the tensor-core kernel (40960 nodes)
+    n0 = 28_500  # just below the automatic switch to the tensor-core kernel (28672 nodes)
     tree = W.prefilled_tree(spec, n0, seed=17, cost_hi=2.0)
     out = []
     for profile in (False, True):
@@ -143,7 +143,7 @@ def test_expand_graph_matches_plain_launches(cuda_lib):
             planner.close()
     (ra, na), (rb, nb) = out
     assert na == nb
-    assert n0 < 40960 < na[0], "the first expansion runs the FP32 kernel, the later ones the tensor cores"
+    assert n0 < 28672 < na[0], "the first expansion runs the FP32 kernel, the later ones the tensor cores"
     for (sa, ia, da), (sb, ib, db) in zip(ra, rb):
         assert sa == sb and ia == ib
         for key in ("samples", "near", "outcome", "controls", "steps"):
