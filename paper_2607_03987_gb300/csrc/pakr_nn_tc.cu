@@ -14,20 +14,22 @@
 // recomputing e on those groups gives the exact argmin.  A row whose candidate ring
 // overflowed, or a tree flagged as leaving the box bound, is rescanned exactly by the whole
 // CTA.  Chunk results merge with a 64-bit atomicMin of (distance bits << 32 | index), as in
-// k_nn.
+// k_nn.  Since a differs from the distance by a per-query constant, the chunks also share a
+// per-query minimum of a (W.nn_amin) and prune their candidates against it.
 //
 // Two CTAs share an SM, each with two accumulators of 128 TMEM columns.  Within a CTA the
 // work is one dependency chain (MMA, commit, readers, release, next MMA) whose mbarrier
 // hand-offs cost on the order of a hundred cycles each; the second CTA's MMAs fill the
 // tensor pipe while the first waits on that chain.
 //
-// Roles (8 warps per CTA):
+// Roles (TcShape<D>::THREADS: 12 warps per CTA for d <= 8, 8 for larger d):
 //   warp 0 lane 0   bulk-copies packed half tiles (T.XT) and f-costs into a ring of stages;
 //   warp 1 lane 0   waits "stage masked" and the release of the accumulator the tile will use
 //                   (tile t - 2's), then issues KT/8 MMAs (M 128, N 128, K 8);
 //   warps 2-3       mask ineligible rows (|x|^2 columns := 2^100), then signal "stage masked";
-//   warps 4-7       read the accumulators (two 64-column tcgen05.ld per tile), group minima,
-//                   candidate rings; one reader thread per query row.
+//   warps 4-        read the accumulators, group minima, candidate rings: for d <= 8 two
+//                   warps per TMEM lane quarter, 64 columns each (two reader threads per query
+//                   row); for larger d one per quarter, all 128 columns.
 // Warps off the MMA thread's chain wait with the suspending mbarrier.try_wait, so that their
 // polls take no issue slots from the readers.  Every wait is bounded (1 s of device time);
 // on timeout the CTA sets ERR_TC_TIMEOUT, stops issuing work and still frees its TMEM.
