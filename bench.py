@@ -7,10 +7,15 @@ append) of the 3D double-integrator workload: 6D state, 50 random boxes,
 nodes and L2 is flushed (a 256 MB write), so every step does the same work
 from DRAM.
 
-Printed JSON line: tree expansions/s (rollouts per second) over all ranks,
-the NN kernel's roofline (FP32 ALU bound), the e2e rate through the C ABI with
+Printed JSON line: tree expansions/s (rollouts per second) over all ranks, the
+rooflines of the nearest-neighbour kernel (tensor bound) and of the
+propagate-collide kernel (FP32 ALU bound), the e2e rate through the C ABI with
 the per-step info read back to the host, p50 time to first solution and the
-AO-x cost after 100 ms, the CPU oracle timed on a bounded sample, clocks.
+AO-x cost after 100 ms on the three planning workloads (with a cost-vs-time
+curve), the batched, adjoint and refinement measurements, a reduced Table 4
+sweep, the CPU oracle timed on a bounded sample (one thread and all host
+cores), and clocks.  Everything that runs the oracle sits in the CPU leg at
+the end (timing, and the oracle's checks of gradients and paths).
 
 ``--impl reference`` times the FP64 CPU oracle on the same workload instead.
 Multi-GPU (torchrun): independent replicas, one per GPU, weak scaling.
@@ -126,10 +131,10 @@ def measured_peaks():
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one tensor-core nearest-neighbour launch
-# (k_nn_tc) on the bench workload (n = 1,000,000 nodes, d = 6) from one ncu capture of the
-# current kernel (read 100.53 MB: the 96 MB packed operand copy, f-costs and the packed rows
-# of the exact resolve's candidate groups; written 3.48 MB).
-NN_DRAM_BYTES_NCU = 100.53e6 + 3.48e6
+# (k_nn_tc) on the bench workload (n = 1,000,000 nodes, d = 6), from the ncu capture named in
+# NN_DRAM_SOURCE.  None when the kernel has changed since that capture.
+NN_DRAM_BYTES_NCU = None
+NN_DRAM_SOURCE = None
 
 # Nominal dense TF32 / BF16 tensor throughput ratio (1.1 / 2.25 PFLOP/s): the TF32 peak is
 # the measured BF16 GEMM rate times this.
@@ -137,22 +142,32 @@ TF32_PER_BF16 = 1.1 / 2.25
 
 
 def nn_flops_per_launch(K, n, d):
-    """Algorithmic FP32 work of one nearest-neighbour pass: a subtract, a
-    multiply and an add per coordinate of every (query, node) pair."""
+    """Algorithmic work of one nearest-neighbour pass, the method's own count: a subtract,
+    a multiply and an add per coordinate of every (query, node) pair."""
     return 3.0 * K * n * d
 
 
-def nn_tc_flops_per_launch(K, n, d):
-    """Algorithmic tensor-core work of the filter: per (query, node) pair the three
-    TF32 partial products of d coordinates and the two |x|^2 columns, 2 flop each."""
-    return 2.0 * K * n * (3 * d + 2)
+def nn_tc_filter_flops_per_launch(K, n, d, kt):
+    """Tensor-core work of the filter as the kernel forms it: per (query, node) pair kt
+    TF32 multiply-adds (the hi/lo partial products and the two |x|^2 columns)."""
+    return 2.0 * K * n * kt
 
 
-def nn_tc_mma_flops_per_launch(K, n, d):
+def nn_tc_mma_flops_per_launch(K, n, d, kt, mma_steps):
     """Tensor-core work as issued: queries padded to 128-row blocks, nodes to 256-node
-    tiles, operand columns to a multiple of 8."""
-    kt = ((3 * d + 2) + 7) // 8 * 8
-    return 2.0 * (-(-K // 128) * 128) * (-(-n // 256) * 256) * kt
+    tiles, mma_steps MMAs of K = 8 per 128 x 128 block."""
+    return 2.0 * (-(-K // 128) * 128) * (-(-n // 256) * 256) * 8 * mma_steps
+
+
+def tc_shape(d):
+    """(columns of the packed node row, MMA k-steps per 128-node stage) of k_nn_tc: the split
+    layout (x_hi, x_lo, |x|^2 hi, lo) with a second query operand against the x_hi columns where
+    it stores fewer columns without more MMAs (d = 3, 5, 6), else (x_hi, x_lo, x_hi, |x|^2)."""
+    joint = ((3 * d + 2) + 7) // 8 * 8
+    split = ((2 * d + 2) + 7) // 8 * 8
+    if split < joint and split // 8 + (d + 7) // 8 <= joint // 8:
+        return split, split // 8 + (d + 7) // 8
+    return joint, joint // 8
 
 
 def nn_uses_tensor_cores(spec, n):
@@ -164,36 +179,147 @@ def nn_uses_tensor_cores(spec, n):
     return mode == 0 and spec["K"] >= 256 and n >= 28672
 
 
+# Algorithmic FP32 work of one propagate-collide substep (an FMA counts 2, an add, multiply or
+# compare 1): the RK4 combination (3 stage points and 3 accumulations of d FMAs, a final add and
+# FMA of d: 15 d), four evaluations of the dynamics (double integrator 0; quadrotor 77 flops
+# and 3 sincos at 20 each, 137), the state-box test (2 d compares), the obstacle tests (2 pdim
+# compares per box), the path-length increment (10) and the heuristic with the prune test (10).
+F_EVAL_FLOPS = {"di2": 0, "di3": 0, "quad12": 137}
+
+
+def propagate_flops_per_substep(spec):
+    d, pdim = spec["d"], spec["pdim"]
+    n_obs = len(spec["boxes"]) + len(spec["spheres"])
+    return 15 * d + 4 * F_EVAL_FLOPS[spec["name"]] + 2 * d + 2 * pdim * n_obs + 10 + 10
+
+
 def nn_bytes_per_launch(n, d):
     """Algorithmic DRAM bytes: every node's d coordinates and its f-cost, once."""
     return 4.0 * n * (d + 1)
 
 
-def cpu_baseline(spec, tree, seed, target_s=10.0):
-    """The FP64 oracle, single-threaded, on a bounded sample of the workload:
-    one expansion with fewer parents on the same 1,000,000-node tree."""
+# ---- the CPU leg: the FP64 oracle as it stands, on the host cores --------------------------
+_ORA = {}
+
+
+def _ora_init(workload, n_prefill, tree_seed):
+    """Pool worker set-up: the oracle problem and the prefilled tree, once per process."""
     import oracle
     from paper_2607_03987_gb300 import workloads as W
 
-    def run(K):
-        s = W.with_sizes(spec, K=K)
-        prob = oracle.OracleProblem(s)
-        prob.set_goal(s["x_goal"])
-        ot = oracle.OracleTree.from_arrays(s["d"], s["m"], s["cap"], tree["states"], tree["controls"],
-                                           tree["parents"], tree["costs"], tree["steps"])
-        t0 = time.perf_counter()
-        oracle.expand(prob, ot, np.inf, seed)
-        return time.perf_counter() - t0
+    spec = W.problem(workload, env_seed=0)
+    tree = W.prefilled_tree(spec, n_prefill, seed=tree_seed)
+    _ORA["spec"] = spec
+    _ORA["tree"] = oracle.OracleTree.from_arrays(spec["d"], spec["m"], spec["cap"], tree["states"],
+                                                 tree["controls"], tree["parents"], tree["costs"], tree["steps"])
+    _ORA["n"] = n_prefill
 
-    K0 = 16
-    t0 = run(K0)
-    K1 = int(max(K0, min(spec["K"], K0 * target_s / max(t0, 1e-3))))
-    t1 = run(K1) if K1 != K0 else t0
-    rollouts = K1 * spec["k"]
-    return {"value": rollouts / t1, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one expansion with {K1} of {spec['K']} parents x {spec['k']} controls on the same "
-                      f"{N_PREFILL}-node tree ({rollouts} rollouts, {t1:.1f} s single-threaded FP64)"}
 
+def _ora_expand(args):
+    """One oracle expansion with K parents from the prefilled tree; (rollouts, seconds)."""
+    import oracle
+    from paper_2607_03987_gb300 import workloads as W
+
+    K, seed = args
+    s = W.with_sizes(_ORA["spec"], K=K)
+    prob = oracle.OracleProblem(s)
+    prob.set_goal(s["x_goal"])
+    ot = _ORA["tree"]
+    ot.T.count = _ORA["n"]
+    t0 = time.perf_counter()
+    oracle.expand(prob, ot, np.inf, seed)
+    return K * s["k"], time.perf_counter() - t0
+
+
+def oracle_pool(workers, tree_seed):
+    """A process pool (spawn: no process is forked from one that holds a CUDA context) whose
+    workers each hold the oracle's copy of the benchmark tree."""
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(workers, initializer=_ora_init, initargs=(WORKLOAD, N_PREFILL, tree_seed))
+    pool.map(_ora_expand, [(1, 0)] * workers)  # every worker has built its tree
+    return pool
+
+
+def cpu_baseline(spec, tree_seed, seed, target_s=10.0):
+    """The FP64 oracle as it stands on a bounded sample of the workload: expansions with fewer
+    parents on the same 1,000,000-node tree, single-threaded and then one process per host
+    core (each expanding its own sample concurrently); about target_s of CPU work each."""
+    cores = os.cpu_count() or 1
+    pool = oracle_pool(cores, tree_seed)
+    try:
+        K0 = 16
+        r0, t0 = pool.apply(_ora_expand, ((K0, seed),))
+        K1 = int(max(K0, min(spec["K"], K0 * target_s / max(t0, 1e-3))))
+        r1, t1 = pool.apply(_ora_expand, ((K1, seed),))
+        single = r1 / t1
+        w0 = time.perf_counter()
+        res = pool.map(_ora_expand, [(K1, seed + 1 + w) for w in range(cores)], chunksize=1)
+        wall = time.perf_counter() - w0
+    finally:
+        pool.close()
+        pool.join()
+    rollouts = sum(r for r, _ in res)
+    return {"value": rollouts / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread_value": single,
+            "sample": f"{cores} processes (all host cores), each one expansion with {K1} of {spec['K']} parents x "
+                      f"{spec['k']} controls on the same {N_PREFILL}-node tree ({rollouts} rollouts in {wall:.1f} s "
+                      f"wall); single-threaded: {r1} rollouts in {t1:.1f} s, FP64"}
+
+
+def oracle_checks(pending):
+    """The oracle's checks of results the GPU measurements produced (run in the CPU leg):
+    relative error of sampled adjoint gradients against the FP64 reverse mode, and an FP64
+    replay of every plain and refined AO-x path (valid at every substep, continuous misses of
+    the substep check counted exactly for the double integrator, in the goal ball, length)."""
+    import oracle
+    from paper_2607_03987_gb300 import refine
+
+    out = {}
+    adj = pending.get("adjoint")
+    if adj:
+        spec = adj["spec"]
+        prob = oracle.OracleProblem(spec)
+        prob.set_goal(spec["x_goal"])
+        w = dict(refine.DEFAULT_WEIGHTS)
+        ow = oracle.traj_params(w_dur=w["w_duration"], w_u=w["w_control"], w_obs=w["w_obstacle"], beta=w["beta"],
+                                margin=w["margin"], w_goal=w["w_goal"], w_len=w["w_length"], len_eps=w["length_eps"])
+        errs = []
+        for x0, U, dU in adj["samples"]:
+            _, dUo, _ = oracle.traj_grad(prob, x0, U, ow)
+            errs.append(float(np.abs(dU - dUo).max() / np.abs(dUo).max()))
+        out["adjoint"] = {"max_rel_grad_error_vs_fp64_oracle": max(errs), "sampled_sequences": len(errs)}
+    for key, paths in pending.get("paths", {}).items():
+        spec = paths["spec"]
+        prob = oracle.OracleProblem(spec)
+        prob.set_goal(spec["x_goal"])
+        summary = {}
+        for kind in ("plain", "refined"):
+            n = valid = in_goal = misses = edges = exempt = 0
+            for x0, U, steps, length in paths[kind]:
+                x = np.asarray(x0, np.float64)
+                g, ok = 0.0, True
+                for e in range(len(steps)):
+                    u = np.asarray(U[e], np.float64)
+                    r = oracle.propagate(prob, x, g, u, int(steps[e]))
+                    if r["collided"]:
+                        if r["face_margin"] < 1e-5:
+                            exempt += 1
+                        else:
+                            ok = False
+                    elif oracle.di_edge_hits_exact(prob, x, u, int(steps[e])):
+                        misses += 1
+                    x, g = r["x_end"], r["cost_end"]
+                    edges += 1
+                n += 1
+                valid += ok
+                pd = spec["pdim"]
+                in_goal += bool(np.linalg.norm(x[:pd] - spec["x_goal"][:pd]) <= spec["goal_r"])
+            summary[kind] = {"paths": n, "valid_at_every_substep": valid, "in_goal": in_goal, "edges": edges,
+                             "face_exempt_edges": exempt, "continuous_misses": misses}
+        out[key] = summary
+    return out
 
 
 def table4_sweep(dev, stream, trials=20, budget_s=1.0):
@@ -343,7 +469,6 @@ def adjoint_bench(dev, stream, T=1024, N=200, reps=20):
     against the FP64 oracle's reverse mode on a sample of sequences."""
     import torch
 
-    import oracle
     from paper_2607_03987_gb300 import pakr, refine
     from paper_2607_03987_gb300 import workloads as W
 
@@ -389,83 +514,147 @@ def adjoint_bench(dev, stream, T=1024, N=200, reps=20):
         torch.cuda.synchronize(dev)
         times[name] = a.elapsed_time(b) / reps
     dUh = dU.cpu().numpy()
-    prob = oracle.OracleProblem(spec)
-    prob.set_goal(spec["x_goal"])
-    ow = oracle.traj_params(w_dur=w["w_duration"], w_u=w["w_control"], w_obs=w["w_obstacle"], beta=w["beta"],
-                            margin=w["margin"], w_goal=w["w_goal"], w_len=w["w_length"], len_eps=w["length_eps"])
-    errs = []
-    for t in range(0, T, T // 8):
-        _, dUo, _ = oracle.traj_grad(prob, x0[t], U[t], ow)
-        errs.append(float(np.abs(dUh[t] - dUo).max() / np.abs(dUo).max()))
+    # sampled sequences for the oracle's check in the CPU leg
+    samples = [(x0[t].copy(), U[t].copy(), dUh[t].copy()) for t in range(0, T, T // 8)]
     planner.close()
+    pending = {"spec": spec, "samples": samples}
     return {"sequences": T, "steps": N, "checkpoint_every": 16, **times,
             "gradients_per_s": T / (times["grad_ms"] * 1e-3),
-            "max_rel_grad_error_vs_fp64_oracle": max(errs), "sampled_sequences": len(errs),
             "workload": "12D quadrotor, dt 0.02, 100 pillars, hover thrust + N(0,0.5), torques U[-0.002,0.002]; "
-                        "cost = duration + 0.1 |u|^2 + softplus(50 (-sdf)) penalty + goal error"}
+                        "cost = duration + 0.1 |u|^2 + softplus(50 (-sdf)) penalty + goal error"}, pending
 
 
 def refined_vs_plain(dev, stream, budget_s=0.1, seeds=10, n_boxes=50):
-    """AO-x path cost after the same wall-clock budget: plain pakr_plan vs
-    planning to a first solution, refining it with the adjoint kernels,
-    tightening the bound to the refined cost, and repeating."""
+    """AO-x path cost after the same wall-clock budget: plain pakr_plan vs AO-x in slices with
+    a gradient refinement of each new best path and the bound tightened to the refined cost
+    (refine.refined_aox).  The paths of both are kept for the oracle's re-check in the CPU leg."""
     from paper_2607_03987_gb300 import pakr, refine
     from paper_2607_03987_gb300 import workloads as W
 
     spec = W.problem("di3", env_seed=0, n_boxes=n_boxes)
     planner = pakr.Planner(spec, device=dev, stream=stream)
     refine.refined_aox(planner, spec, 0.05, seed=999)  # warm-up (graphs, torch kernels)
-    plain, refined, rounds = [], [], []
+    plain, refined, gains, t_plain, t_ref = [], [], [], [], []
+    pending = {"spec": spec, "plain": [], "refined": []}
     for sd in range(seeds):
         t0 = time.perf_counter()
         r = planner.plan(spec["x_init"], spec["x_goal"], budget_s=budget_s, seed=sd)
+        t_plain.append(time.perf_counter() - t0)
         plain.append(float(r["cost"]))
-        c, hist, gain = refine.refined_aox(planner, spec, budget_s, seed=sd)
+        if r["n_solutions"]:
+            pending["plain"].append((r["states"][0], r["controls"], r["steps"], float(r["cost"])))
+        t0 = time.perf_counter()
+        c, hist, gain, best = refine.refined_aox(planner, spec, budget_s, seed=sd)
+        t_ref.append(time.perf_counter() - t0)
         refined.append(c)
-        rounds.append(gain)
+        gains.append(gain)
+        if best is not None:
+            pending["refined"].append((best["x0"], best["controls"], best["steps"], c))
     planner.close()
     lb = float(np.linalg.norm(spec["x_goal"][:3] - spec["x_init"][:3]) - spec["goal_r"])
     return {"budget_s": budget_s, "seeds": seeds, "plain_cost_p50": float(np.median(plain)),
             "refined_cost_p50": float(np.median(refined)), "refined_lower_in": int(sum(a < b for a, b in
                                                                                      zip(refined, plain))),
-            "plain_costs": plain, "refined_costs": refined, "refinement_gain_p50": float(np.median(rounds)),
+            "plain_costs": plain, "refined_costs": refined, "refinement_gain_p50": float(np.median(gains)),
+            "wall_s_p50": {"plain": float(np.median(t_plain)), "refined": float(np.median(t_ref))},
             "straight_line_lower_bound": lb,
-            "workload": f"di3 (3D double integrator, {n_boxes} boxes, path-length cost), host wall-clock budget per seed"}
+            "workload": f"di3 (3D double integrator, {n_boxes} boxes, path-length cost), host wall-clock budget "
+                        f"per seed"}, pending
+
+
+def planning_metrics(dev, stream, name, ttfs_trials, aox_trials, rank=0, aox_budget_s=0.1):
+    """Paper Tables 1-2 analogues on one planning workload: p50 time to the first solution
+    (device AO-x graph stopped at the first solution; device clock, and host wall clock through
+    pakr_plan), and the AO-x best cost after a 100 ms device-time budget with its cost-vs-time
+    curve (the median over seeds of the best cost found by each time; Fig. 2 analogue)."""
+    from paper_2607_03987_gb300 import pakr
+    from paper_2607_03987_gb300 import workloads as W
+
+    spec = W.problem(name, env_seed=0)
+    planner = pakr.Planner(spec, device=dev, stream=stream)
+    planner.plan(spec["x_init"], spec["x_goal"], budget_s=1.0, seed=12345, stop_at_first=True)  # builds the graph
+    ttfs_dev, ttfs_host, iters, solved = [], [], [], 0
+    d2h = []
+    for sd in range(ttfs_trials):
+        t0 = time.perf_counter()
+        r = planner.plan(spec["x_init"], spec["x_goal"], budget_s=2.0, seed=sd + 1000 * rank, stop_at_first=True)
+        th = time.perf_counter() - t0
+        if r["n_solutions"]:
+            solved += 1
+            ttfs_dev.append(r["t_first_solution_s"] * 1e3)
+            ttfs_host.append(th * 1e3)
+            iters.append(r["iterations_first_solution"])
+            ne = r["n_edges"]
+            d2h.append(200 + 20 + (ne + 1) * spec["d"] * 4 + ne * (spec["m"] * 4 + 4))
+    grid_ms = [1, 2, 5, 10, 20, 50, 100]
+    costs, n_sol, curves = [], [], []
+    for sd in range(aox_trials):
+        r = planner.plan(spec["x_init"], spec["x_goal"], budget_s=aox_budget_s, seed=sd + 1000 * rank)
+        costs.append(float(r["cost"]))
+        n_sol.append(r["n_solutions"])
+        ht = np.asarray(r["history_time_s"]) * 1e3
+        hc = np.asarray(r["history_cost"], np.float64)
+        curves.append([float(hc[ht <= t].min()) if np.any(ht <= t) else float("inf") for t in grid_ms])
+    planner.close()
+    curves = np.asarray(curves)
+
+    def q(v, p):
+        return float(np.percentile(v, p)) if len(v) else None
+
+    pd = spec["pdim"]
+    lb = float(np.linalg.norm(spec["x_goal"][:pd] - spec["x_init"][:pd]) - spec["goal_r"])
+    finite = [c for c in costs if np.isfinite(c)]
+    return {
+        "workload": f"{name}: {spec['K']} parents x {spec['k']} controls, cap {spec['cap']}, "
+                    f"{len(spec['boxes'])} boxes, fresh tree from the start to the goal ball r={spec['goal_r']:.2f}",
+        "time_to_first_solution_ms": {"p25": q(ttfs_dev, 25), "p50": q(ttfs_dev, 50), "p75": q(ttfs_dev, 75),
+                                      "host_p50": q(ttfs_host, 50), "iterations_p50": q(iters, 50),
+                                      "trials": ttfs_trials, "success_rate": solved / max(ttfs_trials, 1)},
+        "aox_path_cost_at_100ms": {"p25": q(finite, 25), "p50": float(np.median(costs)) if costs else None,
+                                   "p75": q(finite, 75), "solved": len(finite), "trials": aox_trials,
+                                   "solutions_p50": q(n_sol, 50), "straight_line_lower_bound": lb},
+        "cost_vs_time_ms": {"t_ms": grid_ms, "best_cost_p50": [float(np.median(curves[:, i])) for i in
+                                                              range(len(grid_ms))] if len(curves) else None,
+                            "solved_fraction": [float(np.mean(np.isfinite(curves[:, i]))) for i in
+                                                range(len(grid_ms))] if len(curves) else None},
+        "_e2e_plan": {"host_ms_p50": q(ttfs_host, 50), "d2h_bytes_mean": float(np.mean(d2h)) if d2h else None},
+    }
+
 
 def run_reference(args):
+    """The FP64 oracle as it stands on the machine's host cores (one process per core, spawn):
+    each step is one round in which every process expands 64 parents of the 1,000,000-node
+    tree; the step's rate is all rollouts over the round's wall time."""
     ws, rank, local = _dist_env()
     if rank != 0:
         return 0
-    import oracle
     from paper_2607_03987_gb300 import workloads as W
 
     spec = W.problem(WORKLOAD, env_seed=0)
-    tree = W.prefilled_tree(spec, N_PREFILL, seed=1)
     K_sample = 64
-    s = W.with_sizes(spec, K=K_sample)
-    prob = oracle.OracleProblem(s)
-    prob.set_goal(s["x_goal"])
-    ot = oracle.OracleTree.from_arrays(s["d"], s["m"], s["cap"], tree["states"], tree["controls"], tree["parents"],
-                                       tree["costs"], tree["steps"])
-    for w in range(args.warmup):
-        ot.T.count = N_PREFILL
-        oracle.expand(prob, ot, np.inf, 1000 + w)
-    times = []
-    for st in range(args.steps):
-        ot.T.count = N_PREFILL
-        t0 = time.perf_counter()
-        oracle.expand(prob, ot, np.inf, st)
-        times.append(time.perf_counter() - t0)
+    cores = os.cpu_count() or 1
+    pool = oracle_pool(cores, tree_seed=1)
+    try:
+        for w in range(args.warmup):
+            pool.map(_ora_expand, [(K_sample, 1000 + 64 * w + c) for c in range(cores)], chunksize=1)
+        times, rollouts = [], 0
+        for st in range(args.steps):
+            t0 = time.perf_counter()
+            res = pool.map(_ora_expand, [(K_sample, 64 * st + c) for c in range(cores)], chunksize=1)
+            times.append(time.perf_counter() - t0)
+            rollouts += sum(r for r, _ in res)
+    finally:
+        pool.close()
+        pool.join()
     total = sum(times)
-    rollouts = K_sample * s["k"] * args.steps
     value = rollouts / total
-    sample = (f"each step one expansion with {K_sample} of {spec['K']} parents x {spec['k']} controls on the "
-              f"{N_PREFILL}-node tree, single-threaded FP64")
+    sample = (f"each step {cores} processes (all host cores), each one expansion with {K_sample} of {spec['K']} "
+              f"parents x {spec['k']} controls on the {N_PREFILL}-node tree, FP64")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -477,20 +666,20 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="pakr", choices=["pakr", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the CPU leg (oracle timing and checks)")
     ap.add_argument("--ttfs-trials", type=int, default=100)
-    ap.add_argument("--aox-trials", type=int, default=20)
+    ap.add_argument("--aox-trials", type=int, default=100)
+    ap.add_argument("--no-planning", action="store_true", help="skip the planning metrics of the three workloads")
     ap.add_argument("--no-sweep", action="store_true", help="skip the tree-size sweep")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-sequential comparison")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint and refinement measurements")
-    ap.add_argument("--table4", action="store_true",
-                    help="add the batch size x branching factor sweep on the 12D quadrotor (Table 4)")
-    ap.add_argument("--table4-trials", type=int, default=20)
+    ap.add_argument("--table4-trials", type=int, default=3,
+                    help="trials per cell of the batch size x branching factor sweep (Table 4); 0 skips it")
     ap.add_argument("--plain-launches", action="store_true",
                     help="launch each kernel of the timed steps separately (per-kernel profilers cannot see "
                          "kernels inside the expansion graph's conditional nodes)")
     ap.add_argument("--only-expand", action="store_true",
-                    help="time the expansion steps only (no e2e, planning metrics or CPU baseline)")
+                    help="time the expansion steps only (no e2e, planning metrics or CPU leg)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -515,6 +704,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
     planner = pakr.Planner(spec, device=dev, stream=stream)
     planner.tree_import(tree, spec["x_goal"])
+    del tree
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
     R = spec["K"] * spec["k"]
 
@@ -528,7 +718,7 @@ def main():
     torch.cuda.synchronize(dev)
 
     # ---- device-timed steps (value): each step is one expansion graph (sample, the nearest-
-    # neighbour kernel the tree size selects, propagate, append) plus the truncation kernel ----
+    # neighbour kernel the tree size selects, propagate, append) ----
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if args.plain_launches:
@@ -536,7 +726,6 @@ def main():
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    appended = []
     for s in range(args.steps):
         planner.tree_truncate(N_PREFILL)
         flush.zero_()
@@ -555,26 +744,31 @@ def main():
     # ---- per-kernel device times: a separate pass with per-launch CUDA events ----
     planner.set_profiling(False)
     planner.set_profiling(True)
+    substeps = []
     for s in range(min(args.steps, 300)):
         planner.tree_truncate(N_PREFILL)
         flush.zero_()
         one_step(20_000 + s)
+        if s < 20:
+            dbg = planner.debug_last_expand()
+            substeps.append(float(np.sum(dbg["steps"][dbg["outcome"] != pakr.ROLLOUT_NO_PARENT])))
     kt = planner.kernel_times()
     planner.set_profiling(False)
+    kernel_ms = {k: v["ms"] / max(v["launches"], 1) for k, v in kt.items()}
 
     if args.only_expand:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                               "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
-                              "kernel_ms_per_step": {k: v["ms"] / max(v["launches"], 1) for k, v in kt.items()},
-                              "gpu_launches": launches, "config": {"workload": WORKLOAD_DESC}}), flush=True)
+                              "kernel_ms_per_step": kernel_ms, "gpu_launches": launches,
+                              "config": {"workload": WORKLOAD_DESC}}), flush=True)
         planner.close()
         if ws > 1:
             dist.destroy_process_group()
         return 0
 
     # ---- e2e through the C ABI: per-step info read back to the host ----
-    e2e_times = []
+    e2e_times, appended = [], []
     for s in range(args.steps):
         planner.tree_truncate(N_PREFILL)
         flush.zero_()
@@ -584,64 +778,56 @@ def main():
         e2e_times.append(time.perf_counter() - t0)
         appended.append(info["n_appended"])
     e2e_value, _, _ = aggregate(R * args.steps, sum(e2e_times))
+    planner.close()
 
-    # ---- roofline of the dominant kernel ----
-    nn = kt["k_nn_tc"] if nn_uses_tensor_cores(spec, N_PREFILL) else kt["k_nn"]
-    nn_ms = nn["ms"] / max(nn["launches"], 1)
+    # ---- rooflines: nearest neighbour (dominant) and propagate-collide ----
     peaks, peak_src = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak_tflops = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
-    fp32_equiv = nn_flops_per_launch(spec["K"], N_PREFILL, spec["d"]) / (nn_ms * 1e-3) / 1e12
-    if nn_uses_tensor_cores(spec, N_PREFILL):
+    fp32_src = (f"FP32 FFMA: {props.multi_processor_count} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz "
+                f"({peak_src} max SM clock)")
+    K, d = spec["K"], spec["d"]
+    tc = nn_uses_tensor_cores(spec, N_PREFILL)
+    nn_ms = kernel_ms["k_nn_tc" if tc else "k_nn"]
+    method_tflops = nn_flops_per_launch(K, N_PREFILL, d) / (nn_ms * 1e-3) / 1e12
+    if tc:
         tf32_peak = float(peaks["bf16_tflops"]) * TF32_PER_BF16
-        achieved = nn_tc_flops_per_launch(spec["K"], N_PREFILL, spec["d"]) / (nn_ms * 1e-3) / 1e12
-        roofline = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
-                    "frac": achieved / tf32_peak, "traffic": NN_DRAM_BYTES_NCU, "kernel": "k_nn_tc",
-                    "traffic_unit": "DRAM bytes read + written per k_nn_tc launch (ncu, this kernel and workload)",
+        kt_cols, mma_steps = tc_shape(d)
+        roofline = {"bound": "tensor", "achieved": method_tflops, "peak": tf32_peak, "unit": "TFLOP/s",
+                    "frac": method_tflops / tf32_peak, "traffic": NN_DRAM_BYTES_NCU, "kernel": "k_nn_tc",
+                    "work": "3 K n d (a subtract, a multiply and an add per coordinate of every query-node pair), "
+                            "the method's own count",
                     "peak_source": f"TF32 dense = {peak_src} BF16 GEMM {float(peaks['bf16_tflops']):.0f} TFLOP/s "
-                                   f"x nominal TF32/BF16 ratio 1.1/2.25",
-                    "work": "2 K n (3d + 2): three TF32 partial products per coordinate and |x|^2 hi, lo",
-                    "mma_issued_tflops": nn_tc_mma_flops_per_launch(spec["K"], N_PREFILL, spec["d"])
+                                   f"x nominal TF32/BF16 ratio 1.1/2.25 (of {peak_src})",
+                    "traffic_unit": "DRAM bytes read + written per k_nn_tc launch",
+                    "traffic_source": NN_DRAM_SOURCE,
+                    "filter_tflops_as_formed": nn_tc_filter_flops_per_launch(K, N_PREFILL, d, kt_cols)
                     / (nn_ms * 1e-3) / 1e12,
-                    "fp32_equivalent_tflops": fp32_equiv,
-                    "fp32_ffma_peak_tflops": fp32_peak_tflops,
-                    "nn_ms_per_launch": nn_ms,
-                    "nn_dram_gbs_algorithmic": nn_bytes_per_launch(N_PREFILL, spec["d"]) / (nn_ms * 1e-3) / 1e9,
-                    "kernel_ms_per_step": {k: v["ms"] / max(v["launches"], 1) for k, v in kt.items()}}
+                    "mma_issued_tflops": nn_tc_mma_flops_per_launch(K, N_PREFILL, d, kt_cols, mma_steps)
+                    / (nn_ms * 1e-3) / 1e12,
+                    "fp32_ffma_peak_tflops": fp32_peak_tflops, "nn_ms_per_launch": nn_ms,
+                    "nn_dram_gbs_algorithmic": nn_bytes_per_launch(N_PREFILL, d) / (nn_ms * 1e-3) / 1e9,
+                    "kernel_ms_per_step": kernel_ms}
     else:
-        roofline = {"bound": "alu", "achieved": fp32_equiv, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-                    "frac": fp32_equiv / fp32_peak_tflops, "traffic": None, "kernel": "k_nn",
-                    "peak_source": f"FP32 FFMA: {props.multi_processor_count} SMs x 128 lanes x 2 flop x "
-                                   f"{sm_mhz:.0f} MHz ({peak_src} max SM clock)",
-                    "nn_ms_per_launch": nn_ms,
-                    "nn_dram_gbs_algorithmic": nn_bytes_per_launch(N_PREFILL, spec["d"]) / (nn_ms * 1e-3) / 1e9,
-                    "kernel_ms_per_step": {k: v["ms"] / max(v["launches"], 1) for k, v in kt.items()}}
+        roofline = {"bound": "alu", "achieved": method_tflops, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                    "frac": method_tflops / fp32_peak_tflops, "traffic": None, "kernel": "k_nn",
+                    "peak_source": fp32_src, "nn_ms_per_launch": nn_ms,
+                    "nn_dram_gbs_algorithmic": nn_bytes_per_launch(N_PREFILL, d) / (nn_ms * 1e-3) / 1e9,
+                    "kernel_ms_per_step": kernel_ms}
+    prop_ms = kernel_ms["k_propagate"]
+    flops_sub = propagate_flops_per_substep(spec)
+    sub_mean = float(np.mean(substeps)) if substeps else R * (spec["s_min"] + spec["s_max"]) / 2
+    prop_tflops = sub_mean * flops_sub / (prop_ms * 1e-3) / 1e12
+    roofline["propagate"] = {
+        "di3": {"bound": "alu", "achieved": prop_tflops, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                "frac": prop_tflops / fp32_peak_tflops, "kernel": "k_propagate", "ms_per_launch": prop_ms,
+                "substeps_per_launch": sub_mean, "flops_per_substep": flops_sub,
+                "work": "sum over rollouts with a parent of the drawn substeps S x (RK4 + dynamics + state box + "
+                        "2 pdim O obstacle compares + path length + heuristic)", "peak_source": fp32_src}}
 
-    # ---- planning metrics: p50 time to first solution, AO-x cost at 100 ms ----
-    plan_spec = W.problem(WORKLOAD, env_seed=0)
-    plan_planner = pakr.Planner(plan_spec, device=dev, stream=stream)
-    ttfs_dev, ttfs_host, solved = [], [], 0
-    plan_planner.plan(plan_spec["x_init"], plan_spec["x_goal"], budget_s=1.0, seed=12345, stop_at_first=True)
-    for sd in range(args.ttfs_trials):
-        t0 = time.perf_counter()
-        r = plan_planner.plan(plan_spec["x_init"], plan_spec["x_goal"], budget_s=2.0, seed=sd + 1000 * rank,
-                              stop_at_first=True)
-        th = time.perf_counter() - t0
-        if r["n_solutions"]:
-            solved += 1
-            ttfs_dev.append(r["t_first_solution_s"] * 1e3)
-            ttfs_host.append(th * 1e3)
-    costs, n_sol = [], []
-    for sd in range(args.aox_trials):
-        r = plan_planner.plan(plan_spec["x_init"], plan_spec["x_goal"], budget_s=0.1, seed=sd + 1000 * rank)
-        costs.append(r["cost"])
-        n_sol.append(r["n_solutions"])
-    plan_planner.close()
-
-    def q(v, p):
-        return float(np.percentile(v, p)) if len(v) else None
-
+    line = None
+    pending = {}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -653,39 +839,64 @@ def main():
                        "parallelism": f"replicas x{ws}"},
             "nodes_appended_per_step": float(np.mean(appended)) if appended else None,
             "roofline": roofline,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 256,
-                    "how": "pakr_expand with the per-step expansion info copied back and the stream "
-                           "synchronised, host wall clock; inputs (tree) resident, bound and seed are launch "
-                           "arguments"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12, "d2h_bytes_per_step": 200,
+                    "how": "pakr_expand through the C ABI on host arguments, host wall clock per step: the cost "
+                           "bound (4 B) and seed (8 B) go to the device as the expansion graph's kernel "
+                           "parameters, the 200-byte control block comes back to the host to fill the caller's "
+                           "pakr_expand_info, the stream is synchronised; the tree stays resident"},
             "gpu_launches": launches,
             "clocks": clk,
-            "p50_time_to_first_solution_ms": q(ttfs_dev, 50),
-            "time_to_first_solution_ms": {"p25": q(ttfs_dev, 25), "p50": q(ttfs_dev, 50), "p75": q(ttfs_dev, 75),
-                                          "host_p50": q(ttfs_host, 50), "trials": args.ttfs_trials,
-                                          "success_rate": solved / max(args.ttfs_trials, 1),
-                                          "workload": "same environment, fresh tree from (0.1,0.1,0.1) to the "
-                                                      "goal ball at (0.9,0.9,0.9) r=0.05, device-resident AO-x "
-                                                      "graph stopped at the first solution"},
-            "aox_path_cost_at_100ms": {"p25": q(costs, 25), "p50": q(costs, 50), "p75": q(costs, 75),
-                                       "solutions_p50": q(n_sol, 50), "trials": args.aox_trials,
-                                       "straight_line_lower_bound": float(np.linalg.norm(
-                                           plan_spec["x_goal"][:3] - plan_spec["x_init"][:3]) - plan_spec["goal_r"])},
         }
+    if not args.no_planning:
+        plans = {}
+        for name in ("di2", "di3", "quad12"):
+            plans[name] = planning_metrics(dev, stream, name, args.ttfs_trials, args.aox_trials, rank)
+        if rank == 0:
+            e2p = plans["di3"].pop("_e2e_plan")
+            for v in plans.values():
+                v.pop("_e2e_plan", None)
+            line["p50_time_to_first_solution_ms"] = plans["di3"]["time_to_first_solution_ms"]["p50"]
+            line["aox_path_cost_at_100ms"] = plans["di3"]["aox_path_cost_at_100ms"]["p50"]
+            line["planning"] = plans
+            line["e2e_plan"] = {"value": e2p["host_ms_p50"], "unit": "ms (p50 time to first solution, host wall "
+                                "clock through pakr_plan, di3)",
+                                "h2d_bytes_per_step": 160, "d2h_bytes_per_step": e2p["d2h_bytes_mean"],
+                                "how": "pakr_plan with host x_init / x_goal (160-byte parameter block copied to the "
+                                       "device), the path, its history and the 200-byte control block copied back"}
+    if rank == 0:
         if not args.no_sweep:
             line["by_tree_size"] = tree_size_sweep(dev, stream)
+            q12 = [r for r in line["by_tree_size"] if r["workload"] == "quad12"]
+            if q12:
+                qspec = W.problem("quad12", env_seed=0)
+                qr = qspec["K"] * qspec["k"]
+                fq = propagate_flops_per_substep(qspec)
+                pm = float(np.median([r["propagate_ms"] for r in q12]))
+                ach = qr * (qspec["s_min"] + qspec["s_max"]) / 2 * fq / (pm * 1e-3) / 1e12
+                roofline["propagate"]["quad12"] = {
+                    "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                    "frac": ach / fp32_peak_tflops, "kernel": "k_propagate", "ms_per_launch": pm,
+                    "substeps_per_launch": qr * (qspec["s_min"] + qspec["s_max"]) / 2, "flops_per_substep": fq,
+                    "work": "R x mean drawn substeps x flops per substep (as for di3); median over the tree sizes "
+                            "of the sweep", "peak_source": fp32_src}
         if not args.no_batched:
             line["batched_256"] = batched_vs_sequential(dev, stream)
         if not args.no_adjoint:
-            line["adjoint_1024x200"] = adjoint_bench(dev, stream)
-            line["refined_aox_100ms"] = refined_vs_plain(dev, stream)
-            line["refined_aox_100ms_cluttered"] = refined_vs_plain(dev, stream, n_boxes=300)
-        if args.table4:
+            line["adjoint_1024x200"], pending["adjoint"] = adjoint_bench(dev, stream)
+            line["refined_aox_100ms"], p1 = refined_vs_plain(dev, stream)
+            line["refined_aox_100ms_cluttered"], p2 = refined_vs_plain(dev, stream, n_boxes=300)
+            pending["paths"] = {"refined_aox_100ms": p1, "refined_aox_100ms_cluttered": p2}
+        if args.table4_trials > 0:
             line["table4_quad12"] = table4_sweep(dev, stream, trials=args.table4_trials)
+        # ---- the CPU leg: the oracle timed on the host cores, and its checks of GPU results ----
         if not args.no_cpu_baseline and ws == 1:
-            line["cpu_baseline"] = cpu_baseline(spec, tree, seed=7)
+            line["cpu_baseline"] = cpu_baseline(spec, tree_seed=1 + rank, seed=7)
+            checks = oracle_checks(pending)
+            if "adjoint" in checks:
+                line["adjoint_1024x200"].update(checks.pop("adjoint"))
+            for key, v in checks.items():
+                line[key]["oracle_recheck"] = v
         print(json.dumps(line), flush=True)
-    planner.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0

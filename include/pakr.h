@@ -85,7 +85,8 @@ typedef enum pakr_heuristic {
 /* Per-rollout outcome of the last expansion (pakr_debug_last_expand). */
 /* Nearest-neighbour kernel choice.  Both give the same result (the exact FP32
  * argmin, lowest index on a tie).  The tensor-core kernel needs a packed
- * operand copy of the tree (4 * (3d + 2 rounded up to 8) bytes per node). */
+ * operand copy of the tree: 4 * (2d + 2 rounded up to 8) bytes per node for
+ * d = 3, 5, 6, and 4 * (3d + 2 rounded up to 8) for d = 4 and 12. */
 typedef enum pakr_nn_mode {
     PAKR_NN_AUTO = 0,           /* tensor cores for trees of >= 28672 nodes when n_parents >= 256, FP32 otherwise */
     PAKR_NN_FP32 = 1,           /* FP32 kernel only; no packed copy is kept */
@@ -121,7 +122,8 @@ typedef struct pakr_problem_desc {
     const float *model_params;  /* PAKR_QUAD12: mass, Ixx, Iyy, Izz, g; NULL = 1, 0.01, 0.01, 0.02, 9.81 */
     int32_t n_parents;          /* K = nearest-neighbour queries per iteration, >= 1 */
     int32_t branching;          /* A = controls propagated per parent, >= 1 */
-    int64_t tree_cap;           /* N = maximum tree size, >= 1, <= 2^31 - 1 */
+    int64_t tree_cap;           /* N = maximum tree size, >= 1, <= 2^31 - 2^20 (32-bit node indices with room
+                                   for the kernels' rounding of node chunks and tiles) */
     int32_t device;             /* CUDA device ordinal */
     void *cuda_stream;          /* cudaStream_t to queue work on; NULL = default stream */
     void *workspace;            /* optional device buffer the library carves all its memory from; NULL = cudaMalloc */
@@ -274,10 +276,13 @@ pakr_status pakr_tree_import(pakr_planner *planner, const pakr_tree_host *tree, 
 
 /* Per-query and per-rollout records of the last pakr_expand, for parity
  * checks: samples (n_parents x d, node-major), near (n_parents nearest-node
- * indices, -1 if none), outcome (n_parents*branching pakr_outcome codes),
+ * indices, -1 if none), outcome (R = n_parents*branching pakr_outcome codes),
+ * goal (R flags: 1 if the rollout's child survived the prune and the
+ * validity checks -- appended or dropped at a full tree -- and its end
+ * position lies in the goal ball, Algorithm 1 goal test; 0 otherwise),
  * controls (R x m) and steps (R).  Any pointer may be NULL.  Synchronises. */
 pakr_status pakr_debug_last_expand(pakr_planner *planner, float *samples, int32_t *near, int8_t *outcome,
-                                   float *controls, int32_t *steps);
+                                   int8_t *goal, float *controls, int32_t *steps);
 
 /* Per-kernel device time accumulated since profiling was last enabled, in
  * milliseconds, measured with CUDA events on the planner's stream around each
@@ -318,7 +323,7 @@ typedef struct pakr_batch_query {
     const float *boxes;         /* n_boxes x (lo[p], hi[p]) */
     int32_t n_spheres;
     const float *spheres;       /* n_spheres x (c[p], r) */
-    int64_t tree_cap;           /* >= 1, <= 2^31 - 1 */
+    int64_t tree_cap;           /* >= 1, <= 2^31 - 2^20 */
 } pakr_batch_query;
 
 /* Launch shape of the persistent kernel: threads per block (128 or 256; a
@@ -420,20 +425,24 @@ pakr_status pakr_traj_check(pakr_planner *planner, const float *x0, const float 
 /* Cost-pruned nearest neighbour that allocates no device memory.
  *
  * The paper has no counterpart of this call: it exists for callers that
- * cannot allocate device memory where they need the search, such as code
- * running while a stream is captured into a CUDA graph, real-time loops that
- * forbid allocation after start-up, or plugins confined to another
- * framework's memory pool.  It runs the same search kernel as pakr_expand's
- * NearestNeighbor step, but its per-query scratch lives in one static device
- * array built into the library (about 512 KB, held on every GPU that loads
- * the library until the process exits) instead of planner memory.
+ * cannot allocate device memory where they need the search, such as
+ * real-time loops that forbid allocation (and the device-wide
+ * synchronisation cudaFree can bring) after start-up, or plugins confined to
+ * another framework's memory pool.  It runs the same search kernel as
+ * pakr_expand's NearestNeighbor step, but its per-query scratch lives in one
+ * static device array built into the library (about 512 KB, held on every
+ * GPU that loads the library until the process exits) instead of planner
+ * memory.
  *
  * For each query i it writes nearest[i] = the index j < n with fcost[j] <
  * bound that minimises the FP32 squared distance sum_k (queries[k*n_queries +
  * i] - states[k*ld + j])^2, the lowest j on a tie, or -1 if no node is
  * eligible; dist2[i] (optional) gets that squared distance (+inf if none).
+ * (pakr_expand ranks the same distances on coordinates centred on the state
+ * box, which round differently: the two can pick different nodes only where
+ * two candidates' distances are within rounding of each other.)
  *   states   device, d x ld floats, coordinate k of node j at states[k*ld + j]
- *   ld, n    row stride and node count, 0 <= n <= ld < 2^31
+ *   ld, n    row stride and node count, 0 <= n <= 2^31 - 2^20, n <= ld < 2^31
  *   d        3, 4, 5, 6 or 12
  *   fcost    device, n floats (node j is eligible iff fcost[j] < bound)
  *   queries  device, d x n_queries floats, coordinate k of query i at
@@ -442,13 +451,15 @@ pakr_status pakr_traj_check(pakr_planner *planner, const float *x0, const float 
  *   nearest  device, n_queries int32; dist2 device, n_queries floats or NULL
  *   cuda_stream  stream to enqueue on (NULL = default stream)
  * Runs on the calling thread's current device and only enqueues work; no
- * cudaMalloc, cudaFree or allocating library call is made.  The first call on
- * a device looks up the scratch array's device address (and loads the
- * library's GPU code if it is not loaded yet); make that first call before any
- * stream capture.  All calls share the one scratch array and each clears what
- * it uses, so calls whose kernels overlap on the GPU (different streams with
- * no ordering between them) race and give wrong results; order them on one
- * stream or with events. */
+ * cudaMalloc, cudaFree or allocating library call is made.  Every call looks
+ * up the scratch array's device address (that lookup allocates nothing once
+ * the library's GPU code is loaded).  The first call on a device also loads
+ * the GPU code of every search variant for every supported d (the set-up
+ * step); make that first call before any stream capture.  All calls share the
+ * one scratch array, which keeps the last call's contents; each call clears
+ * what it uses, but calls whose kernels overlap on the GPU (different streams
+ * with no ordering between them) race and give wrong results: order them on
+ * one stream or with events. */
 pakr_status pakr_nearest_static(const float *states, int64_t ld, int64_t n, int32_t d, const float *fcost,
                                 float bound, const float *queries, int32_t n_queries, int32_t *nearest,
                                 float *dist2, void *cuda_stream);

@@ -948,9 +948,8 @@ void ora_dynamics_vjp(const ora_problem *P, const double *x, const double *u, co
     }
 }
 
-/* Smallest signed distance from p to the obstacles (boxes: exact box SDF;
- * spheres: |p - c| - r) summed over every obstacle is not what the penalty
- * needs; this returns the SDF of one obstacle given by index, see below. */
+/* Exact signed distance from p to one box [lo, hi] (negative inside) and its
+ * gradient in p. */
 static double box_sdf(int pd, const double *lo, const double *hi, const double *p, double *grad)
 {
     double q[3], out2 = 0.0, qmax = -INFINITY;
@@ -1021,23 +1020,6 @@ static double obstacle_penalty(const ora_problem *P, const ora_traj_params *w, c
             grad[a] += dist > 0 ? -s * (p[a] - c[a]) / dist : 0.0;
     }
     return total;
-}
-
-double ora_obstacle_sdf(const ora_problem *P, const double *p, double *grad)
-{
-    /* signed distance to the nearest obstacle (diagnostic) */
-    int pd = P->pdim;
-    double best = INFINITY, g[3];
-    for (int b = 0; b < P->n_boxes; ++b) {
-        const double *lo = P->boxes + (size_t)b * 2 * pd, *hi = lo + pd;
-        double sdf = box_sdf(pd, lo, hi, p, g);
-        if (sdf < best) {
-            best = sdf;
-            for (int a = 0; a < pd; ++a)
-                grad[a] = g[a];
-        }
-    }
-    return best;
 }
 
 double ora_traj_cost(const ora_problem *P, const double *x0, const double *U, int N, const ora_traj_params *w,

@@ -165,9 +165,15 @@ double ora_traj_grad(const ora_problem *P, const double *x0, const double *U, in
                      double *dU, double *dx0);
 void ora_dynamics_vjp(const ora_problem *P, const double *x, const double *u, const double *a, double *gx,
                       double *gu);
-double ora_obstacle_sdf(const ora_problem *P, const double *p, double *grad);
 
-/* --- validation-only dense re-checks --- */
+/* --- validation-only dense re-checks (Sec. IV-A checks validity at the
+ * integration substeps only; these look between them) ---
+ * ora_recheck_edge_dense: re-integrates the edge with RK4 at dt/sub and
+ * returns 1 if any of the S*sub fine states is invalid (sub = 1 is the
+ * planner's own substep check).
+ * ora_di_edge_hits_exact: double integrator only; 1 if the continuous
+ * closed-form edge p(t) = p0 + v0 t + u t^2/2, t in (0, S dt], touches an
+ * obstacle box or leaves the state box (spheres: dense check at dt/64). */
 int ora_recheck_edge_dense(const ora_problem *P, const double *x0, const double *u, int S, int sub);
 int ora_di_edge_hits_exact(const ora_problem *P, const double *x0, const double *u, int S);
 

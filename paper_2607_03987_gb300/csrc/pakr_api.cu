@@ -70,17 +70,110 @@ constexpr int64_t kMaxPlanIterations = 10000000;  // hard bound on the device-re
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Uniform grid over the position box for the per-substep obstacle test: each cell lists the
+// obstacles whose bounding box reaches it (cell ranges from obstacle_cell, the function the
+// device applies to points, so the lists are exact), and a substep tests only its cell's list.
+// Chosen among a few resolutions for the fewest expected tests per point (list entries per
+// cell), within the shared memory k_propagate stages; none when it would not save at least half
+// of the tests (few obstacles, or obstacles as large as the box).
+struct ObstacleGrid {
+    int g = 0, cells = 0;
+    float lo[3] = {0.f, 0.f, 0.f}, inv[3] = {0.f, 0.f, 0.f};
+    std::vector<int> start;
+    std::vector<unsigned short> items;
+};
+
+constexpr int kPropSmemBudget = 46 * 1024;  // dynamic shared memory of k_propagate (default limit 48 KB)
+
+ObstacleGrid build_obstacle_grid(const pakr_problem_desc *d, const DimInfo &di)
+{
+    ObstacleGrid best;
+    const int pd = di.pdim, nb = d->n_boxes, ns = d->n_spheres, n_obs = nb + ns;
+    if (n_obs < 4 || pd < 2 || pd > 3)
+        return best;
+    // bounding boxes: boxes as given; spheres widened by a margin that covers the rounding of
+    // the device's FP32 test |p - c|^2 <= r^2
+    std::vector<float> blo((size_t)n_obs * pd), bhi((size_t)n_obs * pd);
+    for (int i = 0; i < nb; ++i)
+        for (int a = 0; a < pd; ++a) {
+            blo[(size_t)i * pd + a] = d->boxes[(size_t)i * 2 * pd + a];
+            bhi[(size_t)i * pd + a] = d->boxes[(size_t)i * 2 * pd + pd + a];
+        }
+    for (int i = 0; i < ns; ++i) {
+        const float *sp = d->spheres + (size_t)i * (pd + 1);
+        const float r = std::fabs(sp[pd]) * (1.f + 1e-4f) + 1e-6f;
+        for (int a = 0; a < pd; ++a) {
+            blo[(size_t)(nb + i) * pd + a] = sp[a] - r;
+            bhi[(size_t)(nb + i) * pd + a] = sp[a] + r;
+        }
+    }
+    float lo[3] = {0.f, 0.f, 0.f}, hi[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < pd; ++a) {
+        lo[a] = d->x_lo[a];
+        hi[a] = d->x_hi[a];
+        if (!(hi[a] > lo[a]))
+            return best;
+    }
+    const int cand3[] = {10, 8, 6, 4}, cand2[] = {32, 24, 16, 8};
+    double best_tests = 0.5 * n_obs;
+    for (int ci = 0; ci < 4; ++ci) {
+        const int g = pd == 3 ? cand3[ci] : cand2[ci];
+        ObstacleGrid G;
+        G.g = g;
+        G.cells = pd == 3 ? g * g * g : g * g;
+        for (int a = 0; a < pd; ++a) {
+            G.lo[a] = lo[a];
+            G.inv[a] = (float)((double)g / ((double)hi[a] - (double)lo[a]));
+        }
+        std::vector<int> count((size_t)G.cells + 1, 0);
+        std::vector<int> r0((size_t)n_obs * 3, 0), r1((size_t)n_obs * 3, 0);
+        size_t items = 0;
+        for (int o = 0; o < n_obs; ++o) {
+            size_t vol = 1;
+            for (int a = 0; a < pd; ++a) {
+                r0[(size_t)o * 3 + a] = obstacle_cell(blo[(size_t)o * pd + a], G.lo[a], G.inv[a], g);
+                r1[(size_t)o * 3 + a] = obstacle_cell(bhi[(size_t)o * pd + a], G.lo[a], G.inv[a], g);
+                vol *= (size_t)(r1[(size_t)o * 3 + a] - r0[(size_t)o * 3 + a] + 1);
+            }
+            items += vol;
+        }
+        const double tests = (double)items / G.cells;
+        if (items > 65535 ||
+            propagate_smem_bytes(nb, ns, G.cells, (int)items) > kPropSmemBudget || !(tests < best_tests))
+            continue;
+        // lists in obstacle order (boxes, then spheres), cells in (z, y, x) order
+        for (int o = 0; o < n_obs; ++o)
+            for (int z = pd == 3 ? r0[(size_t)o * 3 + 2] : 0; z <= (pd == 3 ? r1[(size_t)o * 3 + 2] : 0); ++z)
+                for (int y = r0[(size_t)o * 3 + 1]; y <= r1[(size_t)o * 3 + 1]; ++y)
+                    for (int x = r0[(size_t)o * 3]; x <= r1[(size_t)o * 3]; ++x)
+                        ++count[(size_t)(z * g + y) * g + x + 1];
+        G.start.assign((size_t)G.cells + 1, 0);
+        for (int c = 0; c < G.cells; ++c)
+            G.start[c + 1] = G.start[c] + count[c + 1];
+        G.items.assign(items, 0);
+        std::vector<int> fill(G.start.begin(), G.start.end() - 1);
+        for (int o = 0; o < n_obs; ++o)
+            for (int z = pd == 3 ? r0[(size_t)o * 3 + 2] : 0; z <= (pd == 3 ? r1[(size_t)o * 3 + 2] : 0); ++z)
+                for (int y = r0[(size_t)o * 3 + 1]; y <= r1[(size_t)o * 3 + 1]; ++y)
+                    for (int x = r0[(size_t)o * 3]; x <= r1[(size_t)o * 3]; ++x)
+                        G.items[fill[(size_t)(z * g + y) * g + x]++] = (unsigned short)o;
+        best_tests = tests;
+        best = std::move(G);
+    }
+    return best;
+}
+
 // Byte offsets of every device buffer inside one allocation.
 struct Layout {
     size_t X, U, cost, fcost, parent, steps, XT;
     size_t xr, nn_key, nn_amin, st_x, st_u, st_cost, st_f, st_steps, st_parent, outcome, goal, block_count;
-    size_t boxes, spheres, ctl, pp;
+    size_t boxes, spheres, grid_start, grid_items, ctl, pp;
     size_t path_nodes, path_x, path_u, path_steps, hist_t, hist_cost, hist_iter;
     size_t total;
 };
 
 Layout make_layout(const DimInfo &di, int64_t cap, int K, int k, int nb, int ns, int path_cap, int hist_cap,
-                   int tc_row_floats)
+                   int tc_row_floats, const ObstacleGrid &grid)
 {
     Layout L{};
     size_t off = 0;
@@ -114,6 +207,8 @@ Layout make_layout(const DimInfo &di, int64_t cap, int K, int k, int nb, int ns,
     L.block_count = take(sizeof(int) * nblk);
     L.boxes = take(sizeof(float4) * 2 * (size_t)nb);
     L.spheres = take(sizeof(float4) * (size_t)ns);
+    L.grid_start = take(sizeof(int) * grid.start.size());
+    L.grid_items = take(sizeof(unsigned short) * grid.items.size());
     L.ctl = take(sizeof(Ctl));
     L.pp = take(sizeof(PlanParams));
     L.path_nodes = take(sizeof(int) * (size_t)(path_cap + 1));
@@ -189,8 +284,8 @@ pakr_status check_desc(const pakr_problem_desc *d, DimInfo *di)
         return fail(PAKR_ERR_INVALID_ARG, "n_parents and branching must be >= 1");
     if ((int64_t)d->n_parents * d->branching > (int64_t)1 << 30)
         return fail(PAKR_ERR_INVALID_ARG, "n_parents * branching too large");
-    if (d->tree_cap < 1 || d->tree_cap > 0x7FFFFFFFLL)
-        return fail(PAKR_ERR_INVALID_ARG, "tree_cap must be in [1, 2^31-1]");
+    if (d->tree_cap < 1 || d->tree_cap > kMaxTreeNodes)
+        return fail(PAKR_ERR_INVALID_ARG, "tree_cap must be in [1, 2^31 - 2^20]");
     if (d->path_cap < 0 || d->history_cap < 0)
         return fail(PAKR_ERR_INVALID_ARG, "path_cap / history_cap must be >= 0");
     if (d->nn_mode < PAKR_NN_AUTO || d->nn_mode > PAKR_NN_TENSOR)
@@ -638,7 +733,7 @@ pakr_status pakr_workspace_size(const pakr_problem_desc *desc, uint64_t *bytes_o
     const int pc = desc->path_cap ? desc->path_cap : 4096;
     const int hc = desc->history_cap ? desc->history_cap : 1024;
     Layout L = make_layout(di, desc->tree_cap, desc->n_parents, desc->branching, desc->n_boxes, desc->n_spheres, pc,
-                           hc, tc_floats(desc, di));
+                           hc, tc_floats(desc, di), build_obstacle_grid(desc, di));
     *bytes_out = L.total + 256;  // slack for aligning the caller's base pointer
     return PAKR_OK;
 }
@@ -667,8 +762,9 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
     p->k = desc->branching;
     p->path_cap = desc->path_cap ? desc->path_cap : 4096;
     p->hist_cap = desc->history_cap ? desc->history_cap : 1024;
+    const ObstacleGrid grid = build_obstacle_grid(desc, di);
     p->lay = make_layout(di, p->cap, p->K, p->k, desc->n_boxes, desc->n_spheres, p->path_cap, p->hist_cap,
-                         tc_floats(desc, di));
+                         tc_floats(desc, di), grid);
 
     auto cleanup = [&](pakr_status s) {
         pakr_destroy(p);
@@ -787,6 +883,23 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
         if (e != cudaSuccess)
             return cleanup(fail(PAKR_ERR_CUDA, "obstacle upload failed: %s", cudaGetErrorString(e)));
     }
+    if (grid.g > 0) {
+        e = cudaMemcpy(b + L.grid_start, grid.start.data(), sizeof(int) * grid.start.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b + L.grid_items, grid.items.data(), sizeof(unsigned short) * grid.items.size(),
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess)
+            return cleanup(fail(PAKR_ERR_CUDA, "obstacle grid upload failed: %s", cudaGetErrorString(e)));
+        P.grid_g = grid.g;
+        P.grid_cells = grid.cells;
+        P.grid_n_items = (int)grid.items.size();
+        for (int a = 0; a < 3; ++a) {
+            P.grid_lo[a] = grid.lo[a];
+            P.grid_inv[a] = grid.inv[a];
+        }
+        P.grid_start = (const int *)(b + L.grid_start);
+        P.grid_items = (const unsigned short *)(b + L.grid_items);
+    }
     e = cudaMemset(p->ctl, 0, sizeof(Ctl));
     if (e != cudaSuccess)
         return cleanup(fail(PAKR_ERR_CUDA, "cudaMemset failed: %s", cudaGetErrorString(e)));
@@ -834,19 +947,19 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
     }
     const int64_t R = (int64_t)p->K * p->k;
     // Lanes per rollout: as many as fit one resident wave of k_propagate on every SM (six
-    // 256-thread blocks, its register limit), but no more lanes than there are obstacles to
-    // split between them.  More lanes shorten each substep's obstacle tests, the kernel's
-    // latency chain (8192 rollouts of the 3D double integrator: 8 lanes 24.6 us, 16 lanes
-    // 23.1 us).
-    const int n_obs = desc->n_boxes + desc->n_spheres;
+    // 256-thread blocks, its register limit), but no more lanes than there are obstacle tests
+    // per substep to split between them (all obstacles, or with the obstacle grid the mean
+    // length of a cell's list).  More lanes shorten each substep's obstacle tests, the
+    // kernel's latency chain; one lane needs no ballot per substep.
+    const double tests = grid.g > 0 ? (double)grid.items.size() / grid.cells : (double)(desc->n_boxes + desc->n_spheres);
     int lanes = 1;
-    while (lanes < kMaxPropLanes && R * lanes * 2 <= (int64_t)sms * 1536 && lanes * 2 <= std::max(1, n_obs))
+    while (lanes < kMaxPropLanes && R * lanes * 2 <= (int64_t)sms * 1536 && lanes * 2 <= std::max(1.0, tests))
         lanes *= 2;
     C.prop_lanes = lanes;
     C.prop_threads = kPropThreads;
     const int64_t rollouts_per_block = kPropThreads / lanes;
     C.prop_blocks = (int)((R + rollouts_per_block - 1) / rollouts_per_block);
-    C.obs_smem_bytes = (int)((2 * desc->n_boxes + desc->n_spheres) * sizeof(float4) + kMaxD * sizeof(float));
+    C.obs_smem_bytes = propagate_smem_bytes(desc->n_boxes, desc->n_spheres, P.grid_cells, P.grid_n_items);
     *out = p;
     g_last_error.clear();
     return PAKR_OK;
@@ -1160,7 +1273,7 @@ pakr_status pakr_tree_import(pakr_planner *p, const pakr_tree_host *t, const flo
 }
 
 pakr_status pakr_debug_last_expand(pakr_planner *p, float *samples, int32_t *near, int8_t *outcome,
-                                   float *controls, int32_t *steps)
+                                   int8_t *goal, float *controls, int32_t *steps)
 {
     if (!p)
         return fail(PAKR_ERR_INVALID_ARG, "planner is NULL");
@@ -1183,6 +1296,8 @@ pakr_status pakr_debug_last_expand(pakr_planner *p, float *samples, int32_t *nea
     }
     if (outcome)
         CUDA_TRY(cudaMemcpy(outcome, p->W.outcome, R, cudaMemcpyDeviceToHost));
+    if (goal)
+        CUDA_TRY(cudaMemcpy(goal, p->W.goal, R, cudaMemcpyDeviceToHost));
     if (controls) {
         std::vector<float> v(R * m);
         CUDA_TRY(cudaMemcpy(v.data(), p->W.st_u, sizeof(float) * v.size(), cudaMemcpyDeviceToHost));

@@ -455,7 +455,7 @@ pakr_status pakr_batch_create(const pakr_problem_desc *base, const pakr_batch_qu
         for (int a = 0; a < d; ++a)
             if (!std::isfinite(qq.x_init[a]) || !std::isfinite(qq.x_goal[a]))
                 return bfail(PAKR_ERR_INVALID_ARG, "query %d: x_init / x_goal must be finite", q);
-        if (qq.tree_cap < 1 || qq.tree_cap > 0x7FFFFFFFLL)
+        if (qq.tree_cap < 1 || qq.tree_cap > kMaxTreeNodes)
             return bfail(PAKR_ERR_INVALID_ARG, "query %d: tree_cap out of range", q);
         if (qq.n_boxes < 0 || qq.n_spheres < 0 || (qq.n_boxes && !qq.boxes) || (qq.n_spheres && !qq.spheres))
             return bfail(PAKR_ERR_INVALID_ARG, "query %d: bad obstacle arrays", q);

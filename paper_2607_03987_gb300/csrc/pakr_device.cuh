@@ -614,11 +614,14 @@ __device__ __forceinline__ int nn_chunk_nodes(int n, int nchunks)
 // Every lane of a rollout's group samples the same control (counter-based
 // Philox) and integrates the same RK4 steps, so their states are identical;
 // the obstacle tests of each substep are split across the group's lanes and
-// combined with a warp ballot.  The substep loop runs to the warp's longest
-// rollout so that every lane reaches each ballot.  With path-length cost and
-// the position heuristic, f = g + h never decreases along an edge (h is
-// 1-Lipschitz in position), so a partial f at or above the bound already
-// decides the prune.
+// combined with a warp ballot (LG > 1; then the substep loop runs to the
+// warp's longest rollout so that every lane reaches each ballot).  The
+// obstacle tests of a substep are those of the position's cell of the
+// obstacle grid when the planner keeps one (every obstacle otherwise), which
+// gives the same answer with a few tests instead of all.  With path-length
+// cost and the position heuristic, f = g + h never decreases along an edge (h
+// is 1-Lipschitz in position), so a partial f at or above a finite bound
+// already decides the prune.
 // ---------------------------------------------------------------------------
 template <int D, int PD>
 __device__ __forceinline__ bool in_state_box(const float *x, const DevProblem &P)
@@ -626,35 +629,62 @@ __device__ __forceinline__ bool in_state_box(const float *x, const DevProblem &P
     bool ok = true;
 #pragma unroll
     for (int a = 0; a < D; ++a)
-        ok = ok && (x[a] >= P.x_lo[a]) && (x[a] <= P.x_hi[a]);
+        ok = ok & (x[a] >= P.x_lo[a]) & (x[a] <= P.x_hi[a]);
     return ok;
 }
 
 template <int PD>
-__device__ __forceinline__ bool hits_obstacle(const float *x, const float4 *boxes, int nb, const float4 *spheres,
-                                              int ns, int first, int stride)
+__device__ __forceinline__ bool in_box(const float *x, const float4 *boxes, int b)
 {
-    for (int b = first; b < nb; b += stride) {
-        const float4 lo = boxes[2 * b], hi = boxes[2 * b + 1];
-        bool inside = (x[0] >= lo.x) & (x[0] <= hi.x) & (x[1] >= lo.y) & (x[1] <= hi.y);
+    const float4 lo = boxes[2 * b], hi = boxes[2 * b + 1];
+    bool inside = (x[0] >= lo.x) & (x[0] <= hi.x) & (x[1] >= lo.y) & (x[1] <= hi.y);
+    if (PD > 2)
+        inside = inside & (x[2] >= lo.z) & (x[2] <= hi.z);
+    return inside;
+}
+
+template <int PD>
+__device__ __forceinline__ bool in_sphere(const float *x, const float4 *spheres, int s)
+{
+    const float4 c = spheres[s];
+    float dd = (x[0] - c.x) * (x[0] - c.x) + (x[1] - c.y) * (x[1] - c.y);
+    if (PD > 2)
+        dd += (x[2] - c.z) * (x[2] - c.z);
+    return dd <= c.w * c.w;
+}
+
+// Obstacle test of position x on this lane's share (first, first + stride, ...) of the
+// obstacles: all of them, or with the obstacle grid only those listed in x's cell.
+template <int PD>
+__device__ __forceinline__ bool hits_obstacle(const float *x, const DevProblem &P, const float4 *boxes, int nb,
+                                              const float4 *spheres, int ns, const int *g_start,
+                                              const unsigned short *g_items, int first, int stride)
+{
+    if (P.grid_g > 0) {
+        const int g = P.grid_g;
+        int c = obstacle_cell(x[0], P.grid_lo[0], P.grid_inv[0], g) + g * obstacle_cell(x[1], P.grid_lo[1], P.grid_inv[1], g);
         if (PD > 2)
-            inside = inside & (x[2] >= lo.z) & (x[2] <= hi.z);
-        if (inside)
-            return true;
+            c += g * g * obstacle_cell(x[2], P.grid_lo[2], P.grid_inv[2], g);
+        const int k1 = g_start[c + 1];
+        for (int k = g_start[c] + first; k < k1; k += stride) {
+            const int o = g_items[k];
+            if (o < nb ? in_box<PD>(x, boxes, o) : in_sphere<PD>(x, spheres, o - nb))
+                return true;
+        }
+        return false;
     }
-    for (int s = first; s < ns; s += stride) {
-        const float4 c = spheres[s];
-        float dd = (x[0] - c.x) * (x[0] - c.x) + (x[1] - c.y) * (x[1] - c.y);
-        if (PD > 2)
-            dd += (x[2] - c.z) * (x[2] - c.z);
-        if (dd <= c.w * c.w)
+    for (int b = first; b < nb; b += stride)
+        if (in_box<PD>(x, boxes, b))
             return true;
-    }
+    for (int s = first; s < ns; s += stride)
+        if (in_sphere<PD>(x, spheres, s))
+            return true;
     return false;
 }
 
-// Rollouts of propagate block vb (blockDim.x / LG rollouts) with the
-// obstacles staged into s_obs (2 n_boxes + n_spheres float4, then the goal).
+// Rollouts of propagate block vb (blockDim.x / LG rollouts) with the obstacles staged into
+// s_obs (2 n_boxes + n_spheres float4, then the goal, then the obstacle grid's cell offsets and
+// lists).
 template <int DYN, int LG>
 __device__ __forceinline__ void propagate_block(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W,
                                                 int vb, float4 *s_obs)
@@ -663,12 +693,20 @@ __device__ __forceinline__ void propagate_block(const DevProblem &P, Ctl *ctl, c
     float4 *s_box = s_obs;
     float4 *s_sph = s_obs + 2 * P.n_boxes;
     float *s_goal = reinterpret_cast<float *>(s_sph + P.n_spheres);
+    int *s_gstart = reinterpret_cast<int *>(s_goal + kMaxD);
+    unsigned short *s_gitems = reinterpret_cast<unsigned short *>(s_gstart + P.grid_cells + 1);
     for (int t = threadIdx.x; t < 2 * P.n_boxes; t += blockDim.x)
         s_box[t] = P.boxes[t];
     for (int t = threadIdx.x; t < P.n_spheres; t += blockDim.x)
         s_sph[t] = P.spheres[t];
     if (threadIdx.x < D)
         s_goal[threadIdx.x] = ctl->x_goal[threadIdx.x];
+    if (P.grid_g > 0) {
+        for (int t = threadIdx.x; t <= P.grid_cells; t += blockDim.x)
+            s_gstart[t] = P.grid_start[t];
+        for (int t = threadIdx.x; t < P.grid_n_items; t += blockDim.x)
+            s_gitems[t] = P.grid_items[t];
+    }
     __syncthreads();
 
     const int R = P.K * P.k;
@@ -678,7 +716,10 @@ __device__ __forceinline__ void propagate_block(const DevProblem &P, Ctl *ctl, c
     const int r = (int)(((long long)vb * blockDim.x + threadIdx.x) / LG);
     const bool have = r < R;
     const float bound = ctl->bound;
-    const bool early = (P.cost == COST_PATH_LENGTH) && (P.heuristic == H_POSITION);
+    // with path-length cost and the position heuristic f never decreases along an edge, so a
+    // partial f at or above a finite bound already decides the prune
+    const bool early = (P.cost == COST_PATH_LENGTH) && (P.heuristic == H_POSITION) &&
+                       (bound < __int_as_float(0x7f800000));
 
     int out = -1;
     bool alive = false;
@@ -725,8 +766,10 @@ __device__ __forceinline__ void propagate_block(const DevProblem &P, Ctl *ctl, c
             }
         }
     }
-    const int s_warp = __reduce_max_sync(0xFFFFFFFFu, alive ? S : 0);
-    for (int s = 1; s <= s_warp; ++s) {
+    // one lane per rollout: each lane runs its own substeps; with several lanes per rollout
+    // every lane of the warp reaches each substep's ballot
+    const int s_last = (LG == 1) ? (alive ? S : 0) : __reduce_max_sync(0xFFFFFFFFu, alive ? S : 0);
+    for (int s = 1; s <= s_last; ++s) {
         const bool act = alive && s <= S;
         bool inb = true;
         if (act) {
@@ -744,10 +787,13 @@ __device__ __forceinline__ void propagate_block(const DevProblem &P, Ctl *ctl, c
             }
             inb = in_state_box<D, PD>(x, P);
         }
-        const bool hit = act && inb && hits_obstacle<PD>(x, s_box, P.n_boxes, s_sph, P.n_spheres, sub, LG);
-        const unsigned any = __ballot_sync(0xFFFFFFFFu, hit);
+        const bool hit = act && inb &&
+                         hits_obstacle<PD>(x, P, s_box, P.n_boxes, s_sph, P.n_spheres, s_gstart, s_gitems, sub, LG);
+        bool any_hit = hit;
+        if constexpr (LG > 1)
+            any_hit = (__ballot_sync(0xFFFFFFFFu, hit) & gmask) != 0u;
         if (act) {
-            if (!inb || (any & gmask)) {
+            if (!inb || any_hit) {
                 out = OUT_COLLIDED;
                 alive = false;
             } else if (early && !(g + heuristic<D, PD>(x, P, s_goal) < bound)) {
@@ -773,8 +819,9 @@ __device__ __forceinline__ void propagate_block(const DevProblem &P, Ctl *ctl, c
             W.st_cost[r] = g;
             W.st_f[r] = f;
             W.st_parent[r] = par;
-            W.goal[r] = in_goal<PD>(x, P, s_goal) ? 1 : 0;
         }
+        // goal flag of every rollout: 1 only for a surviving child in the goal ball
+        W.goal[r] = (out == OUT_APPENDED && in_goal<PD>(x, P, s_goal)) ? 1 : 0;
         W.outcome[r] = (int8_t)out;
     }
     const int n_cand = __syncthreads_count(leader && out == OUT_APPENDED);

@@ -21,6 +21,10 @@ enum { MODE_EXPAND = 0, MODE_PLAN = 1 };
 enum { ERR_PATH_CYCLE = 1, ERR_BAD_PARENT = 2, ERR_TC_TIMEOUT = 4 };
 constexpr int kTcCtasPerSm = 2;  // resident tensor-core nearest-neighbour CTAs per SM
 constexpr int kMaxPropLanes = 16;  // lanes per rollout in k_propagate at most
+// Largest tree (and nearest-neighbour node count) the kernels take: their node indices and
+// chunk arithmetic are 32-bit, and rounding a chunk or a tile up past the last node adds at
+// most a few thousand, so 2^20 below 2^31 leaves room for every rounding.
+constexpr long long kMaxTreeNodes = (1LL << 31) - (1LL << 20);
 
 // Problem constants, passed to every kernel by value.
 struct DevProblem {
@@ -42,7 +46,45 @@ struct DevProblem {
     float tc_c[kMaxD];
     float tc_xbox2;
     int tc_min_n = 0x7FFFFFFF;
+    // obstacle grid over the position box (grid_g = 0: none, every obstacle is tested): cell
+    // index per position axis a is obstacle_cell(p_a, grid_lo[a], grid_inv[a], grid_g), cells
+    // numbered (z * g + y) * g + x; cell c lists obstacles grid_items[grid_start[c] ..
+    // grid_start[c + 1]) (box b as b, sphere s as n_boxes + s), every obstacle that can hold a
+    // point of that cell
+    int grid_g = 0, grid_cells = 0, grid_n_items = 0;
+    float grid_lo[3] = {0.f, 0.f, 0.f}, grid_inv[3] = {0.f, 0.f, 0.f};
+    const int *grid_start = nullptr;
+    const unsigned short *grid_items = nullptr;
 };
+
+// Shared memory k_propagate stages: the obstacles, the goal and the obstacle grid.
+__host__ __device__ inline int propagate_smem_bytes(int n_boxes, int n_spheres, int grid_cells, int grid_n_items)
+{
+    int b = 16 * (2 * n_boxes + n_spheres) + 4 * kMaxD;
+    if (grid_cells > 0)
+        b += 4 * (grid_cells + 1) + 2 * ((grid_n_items + 1) / 2 * 2);
+    return b;
+}
+
+// Cell index of coordinate v on one axis of the obstacle grid: fl(fl(v - lo) * inv) truncated
+// and clamped to [0, g - 1].  Every step is monotone in v, so a point inside an obstacle's
+// bounding box [b_lo, b_hi] always falls in a cell between cell(b_lo) and cell(b_hi): the host
+// lists each obstacle in exactly that range with this same function, and the device test of a
+// point against its cell's list gives the same answer as testing every obstacle.
+__host__ __device__ __forceinline__ int obstacle_cell(float v, float lo, float inv, int g)
+{
+#ifdef __CUDA_ARCH__
+    const float t = __fmul_rn(__fsub_rn(v, lo), inv);
+#else
+    const float d = v - lo;
+    const float t = d * inv;
+#endif
+    if (!(t >= 0.f))
+        return 0;
+    if (t >= (float)g)
+        return g - 1;
+    return (int)t;
+}
 
 // Dimension-major tree arrays.
 struct DevTree {
@@ -149,7 +191,7 @@ cudaError_t launch_nn_fp32(const DevProblem &P, const Ctl *ctl, const DevTree &T
 cudaError_t launch_nn_tc(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
                          cudaStream_t s);
 cudaError_t launch_tc_pack(const DevProblem &P, Ctl *ctl, const DevTree &T, int count, cudaStream_t s);
-int tc_operand_floats(int d);  // floats per packed node row (3d + 2 rounded up to 8)
+int tc_operand_floats(int d);  // floats per packed node row (2d + 2 or 3d + 2 rounded up to 8, pakr_tc.cuh)
 cudaError_t tc_configure(const DevProblem &P);
 cudaError_t launch_propagate(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
                              cudaStream_t s);
@@ -182,5 +224,7 @@ pakr_status fill_problem(const pakr_problem_desc *desc, DevProblem *P, int *d, i
 
 // Occupancy-derived sizes (pakr_kernels.cu).
 int nn_blocks_per_sm(int d, int variant);
+// Loads every k_nn instantiation's GPU code on the current device (pakr_kernels.cu).
+cudaError_t nn_preload_all();
 
 }  // namespace pakr

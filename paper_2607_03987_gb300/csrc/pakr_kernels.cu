@@ -341,6 +341,35 @@ static int nn_occ(int variant)
     return nb;
 }
 
+// Loads the GPU code of every k_nn instantiation (three variants for each supported state
+// dimension) by querying its attributes, so that a later first launch of any of them loads
+// nothing.
+template <int D>
+static cudaError_t nn_preload_d()
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_nn<D, 1, 64, kNnTile, kNnGroup>);
+    if (e == cudaSuccess)
+        e = cudaFuncGetAttributes(&a, k_nn<D, 1, 128, kNnTile, kNnGroup>);
+    if (e == cudaSuccess)
+        e = cudaFuncGetAttributes(&a, k_nn<D, 2, 256, kNnTile, kNnGroup>);
+    return e;
+}
+
+cudaError_t nn_preload_all()
+{
+    cudaError_t e = nn_preload_d<3>();
+    if (e == cudaSuccess)
+        e = nn_preload_d<4>();
+    if (e == cudaSuccess)
+        e = nn_preload_d<5>();
+    if (e == cudaSuccess)
+        e = nn_preload_d<6>();
+    if (e == cudaSuccess)
+        e = nn_preload_d<12>();
+    return e;
+}
+
 int nn_blocks_per_sm(int d, int variant)
 {
     switch (d) {

@@ -27,12 +27,16 @@
 //   warp 1 lane 0   waits "stage masked" and the release of the accumulator the tile will use
 //                   (tile t - 2's), then issues KT/8 MMAs (M 128, N 128, K 8);
 //   warps 2-3       mask ineligible rows (|x|^2 columns := 2^100), then signal "stage masked";
-//   warps 4-        read the accumulators, group minima, candidate rings: for d <= 8 two
+//   warps 4-        read the accumulators' 16-node group minima with TMEM loads that reduce
+//                   (tcgen05.ld.red min, sm_103a) and keep candidate rings: for d <= 8 two
 //                   warps per TMEM lane quarter, 64 columns each (two reader threads per query
 //                   row); for larger d one per quarter, all 128 columns.
 // Warps off the MMA thread's chain wait with the suspending mbarrier.try_wait, so that their
 // polls take no issue slots from the readers.  Every wait is bounded (1 s of device time);
-// on timeout the CTA sets ERR_TC_TIMEOUT, stops issuing work and still frees its TMEM.
+// on timeout the CTA sets ERR_TC_TIMEOUT and stops issuing work.  Before the CTA frees its
+// TMEM and leaves, the loader waits (bounded) until every bulk copy it issued has landed and
+// the MMA thread waits (bounded) on a final commit that follows every MMA it issued, so no
+// asynchronous copy or MMA still writes shared memory or TMEM after the CTA is gone.
 #include "pakr_device.cuh"
 #include "pakr_tc.cuh"
 
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
     float *ring_val = reinterpret_cast<float *>(tc_smem + S::A_BYTES + NST * (S::STAGE_BYTES + S::F_BYTES));
     int *ring_grp = reinterpret_cast<int *>(ring_val + kTcRing * S::READERS);
     __shared__ __align__(8) unsigned long long s_loaded[NST], s_full[NST], s_free[NST];
-    __shared__ __align__(8) unsigned long long s_done[kTcAcc], s_empty[kTcAcc];
+    __shared__ __align__(8) unsigned long long s_done[kTcAcc], s_empty[kTcAcc], s_drain;
     __shared__ uint32_t s_tbase;
     __shared__ volatile int s_abort;
     __shared__ int s_nflag, s_flag_qid[kTcM], s_ovf[kTcM];
@@ -190,18 +194,24 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
             mbar_init(smem_u32(&s_done[i]), 1);
             mbar_init(smem_u32(&s_empty[i]), S::READERS / 32);
         }
+        mbar_init(smem_u32(&s_drain), 1);
         fence_mbar_init();
         s_abort = 0;
         s_nflag = 0;
     }
     if (tid < kTcM) {
         s_ovf[tid] = 0;
-        // query row: -2 (q - c) split as hi (against x_hi), hi (against x_lo), lo (against x_hi); 1, 1
+        // query operand: -2 (q - c) split as hi (against x_hi), hi (against x_lo) and lo (against
+        // x_hi), and 1, 1 against |x|^2 hi, lo.  Split layout: (hi, hi, 1, 1) over the node row and
+        // (lo) in the second operand; joint layout: (hi, hi, lo, 1, 1) in one row.
         const int q = qbase + tid;
-        float row[KT];
+        float row[KT], row2[S::KA2 > 0 ? S::KA2 : 1];
 #pragma unroll
         for (int k = 0; k < KT; ++k)
             row[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < (S::KA2 > 0 ? S::KA2 : 1); ++k)
+            row2[k] = 0.f;
         if (q < K) {
 #pragma unroll
             for (int a = 0; a < D; ++a) {
@@ -209,15 +219,24 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
                 const float hi = tf32_trunc(v);
                 row[a] = hi;
                 row[D + a] = hi;
-                row[2 * D + a] = tf32_trunc(v - hi);
+                if constexpr (S::SPLIT)
+                    row2[a] = tf32_trunc(v - hi);
+                else
+                    row[2 * D + a] = tf32_trunc(v - hi);
             }
-            row[3 * D] = 1.f;
-            row[3 * D + 1] = 1.f;
+            row[S::NORM] = 1.f;
+            row[S::NORM + 1] = 1.f;
         }
 #pragma unroll
         for (int c = 0; c < KT / 4; ++c)
             *reinterpret_cast<float4 *>(sA + tc_off<D>(tid, 4 * c)) =
                 make_float4(row[4 * c], row[4 * c + 1], row[4 * c + 2], row[4 * c + 3]);
+        if constexpr (S::SPLIT) {
+#pragma unroll
+            for (int c = 0; c < S::KA2 / 4; ++c)
+                *reinterpret_cast<float4 *>(sA + S::A1_BYTES + tc_off2<D>(tid, 4 * c)) =
+                    make_float4(row2[4 * c], row2[4 * c + 1], row2[4 * c + 2], row2[4 * c + 3]);
+        }
         fence_async_smem();
     }
     tc_fence_before();
@@ -240,6 +259,7 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
     } else if (warp == kTcLoadWarp) {
         if (lane == 0) {
             const uint32_t sB = smem_u32(sB0), sF = smem_u32(sF0);
+            int issued = 0;
             for (int t = 0; t < ntiles && !s_abort; ++t) {
                 const int b = t % NST;
                 if (t >= NST && !mbar_wait_suspend(smem_u32(&s_free[b]), ((t - NST) / NST) & 1, kWaitNs)) {
@@ -257,7 +277,17 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
                              (size_t)(h & 1) * S::STAGE_BYTES,
                          S::STAGE_BYTES, bar);
                 bulk_g2s(sF + b * S::F_BYTES, T.fcost + j0, fbytes, bar);
+                issued = t + 1;
             }
+            // Drain: every copy this lane issued has landed before the CTA can leave (after an
+            // abort nobody may have waited for the last stages).  A stage is re-armed only after
+            // its previous phase was consumed, so the last phase armed per stage is the only one
+            // that can still be open.
+            for (int t = issued > NST ? issued - NST : 0; t < issued; ++t)
+                if (!mbar_wait_suspend(smem_u32(&s_loaded[t % NST]), (t / NST) & 1, kWaitNs)) {
+                    s_abort = 1;
+                    atomicOr(&ctl->err, ERR_TC_TIMEOUT);
+                }
         }
         __syncwarp();
     } else if (warp >= kTcPatch0 && warp < kTcReader0) {
@@ -277,8 +307,8 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
                     const int j = start + t * kTcBN + r;
                     if (!(j < end && sF0[b * kTcBN + r] < bound)) {
                         unsigned char *rowp = sB0 + b * S::STAGE_BYTES;
-                        *reinterpret_cast<float *>(rowp + tc_off<D>(r, 3 * D)) = kTcSentinel;
-                        *reinterpret_cast<float *>(rowp + tc_off<D>(r, 3 * D + 1)) = 0.f;
+                        *reinterpret_cast<float *>(rowp + tc_off<D>(r, S::NORM)) = kTcSentinel;
+                        *reinterpret_cast<float *>(rowp + tc_off<D>(r, S::NORM + 1)) = 0.f;
                         wrote = true;
                     }
                 }
@@ -295,6 +325,7 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
             // descriptors of stage 0 and k-step 0; the start-address field (address / 16, 14 bits)
             // takes the stage and k-step offsets directly (shared addresses stay below 256 KB)
             const uint64_t adesc = smem_desc(smem_u32(sA), S::LBO, S::SBO);
+            const uint64_t adesc2 = S::SPLIT ? smem_desc(smem_u32(sA + S::A1_BYTES), S::LBO, S::SBO2) : 0ull;
             const uint64_t bdesc = smem_desc(smem_u32(sB0), S::LBO, S::SBO);
             // no per-tile poll of the abort flag (a shared-memory load that queues behind the
             // tile traffic): the masking warps signal every stage even after an abort, and a
@@ -328,6 +359,11 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
                     for (int s = 1; s < KT / 8; ++s)
                         mma_tf32_ss_c<true>(dt, adesc + (uint64_t)((2 * S::LBO * s) >> 4),
                                             bd + (uint64_t)((2 * S::LBO * s) >> 4), idesc);
+                    // split layout: the lo part of the query against the x_hi columns
+#pragma unroll
+                    for (int s = 0; s < S::KA2 / 8; ++s)
+                        mma_tf32_ss_c<true>(dt, adesc2 + (uint64_t)((2 * S::LBO * s) >> 4),
+                                            bd + (uint64_t)((2 * S::LBO * s) >> 4), idesc);
                     mma_commit(free0 + st8);
                     mma_commit(done0 + 8 * ac);
                     st8 += 8;
@@ -341,6 +377,14 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
                 if (!live)
                     break;
                 epar ^= 1u;
+            }
+            // Drain: a final commit completes once every MMA issued above has finished, so no MMA
+            // still writes the accumulators when TMEM is freed, also after an abort that left
+            // accumulators unread.
+            mma_commit(smem_u32(&s_drain));
+            if (!mbar_wait_bounded(smem_u32(&s_drain), 0, kWaitNs)) {
+                s_abort = 1;
+                atomicOr(&ctl->err, ERR_TC_TIMEOUT);
             }
         }
         __syncwarp();
@@ -376,42 +420,20 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
             constexpr int NG = CW / kTcG;      // 16-node groups it reduces per tile
             const uint32_t tcol = tbase + (uint32_t)(b * kTcBN + CW * half) + ((uint32_t)(32 * quarter) << 16);
             const int gbase = start + t * kTcBN + CW * half;
-            // minima of this reader's 16-node groups: two loads of CW / 2 columns, the accumulator
-            // is released after the second; one branch per tile (the candidate test rarely passes
-            // once the running minimum has settled, and a branch per group would stall the warp
-            // on every minimum tree)
+            // minima of this reader's 16-node groups, then the accumulator is released; one branch
+            // per tile (the candidate test rarely passes once the running minimum has settled)
+            // the group minima come straight from the TMEM loads (min reduction, sm_103a): one
+            // load per 16-node group, no ALU work on the values
             float m[NG];
-            if constexpr (S::RH == 2) {
-                float v[32];
-                __syncwarp();
-                tmem_ld32(tcol, v);
-                m[0] = min16(v);
-                m[1] = min16(v + 16);
-                __syncwarp();
-                tmem_ld32(tcol + 32, v);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0)
-                    mbar_arrive(smem_u32(&s_empty[b]));
-                m[2] = min16(v);
-                m[3] = min16(v + 16);
-            } else {
-                float v[64];
-                __syncwarp();
-                tmem_ld64(tcol, v);
 #pragma unroll
-                for (int h4 = 0; h4 < 4; ++h4)
-                    m[h4] = min16(v + 16 * h4);
+            for (int h = 0; h < NG; ++h) {
                 __syncwarp();
-                tmem_ld64(tcol + 64, v);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0)
-                    mbar_arrive(smem_u32(&s_empty[b]));
-#pragma unroll
-                for (int h4 = 0; h4 < 4; ++h4)
-                    m[4 + h4] = min16(v + 16 * h4);
+                m[h] = tmem_ldred_min16(tcol + 16 * h);
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(smem_u32(&s_empty[b]));
             if ((t & 31) == 31 && pub) {
                 const float g = tc_unord(gkey);  // the value read one period ago
                 if (g < m1)
@@ -581,7 +603,7 @@ cudaError_t launch_tc_pack(const DevProblem &P, Ctl *ctl, const DevTree &T, int 
 
 int tc_operand_floats(int d)
 {
-    return ((3 * d + 2) + 7) / 8 * 8;
+    return tc_node_cols(d);
 }
 
 }  // namespace pakr

@@ -2,14 +2,14 @@
 // search for callers that may not allocate device memory.
 //
 // Some callers cannot call cudaMalloc at the point where they need a nearest
-// neighbour: code that runs while a stream is being captured into a CUDA graph,
-// real-time control loops that forbid allocation after start-up, and plugins
-// that live inside another framework's memory pool.  They own their inputs and
-// outputs; what they cannot provide is the library's per-query scratch (the
-// packed distance / index keys that the node chunks merge into, plus the two
-// scalars the search kernel reads).  This file keeps that scratch in one
-// file-scope device array instead, sized for kStaticMaxQueries queries; every
-// GPU that loads the library holds it until the process exits.
+// neighbour: real-time control loops that forbid allocation (and the device-wide
+// synchronisation cudaFree can bring) after start-up, and plugins that live
+// inside another framework's memory pool and may only use what it hands them.
+// They own their inputs and outputs; what they cannot provide is the library's
+// per-query scratch (the packed distance / index keys that the node chunks merge
+// into, plus the two scalars the search kernel reads).  This file keeps that
+// scratch in one file-scope device array instead, sized for kStaticMaxQueries
+// queries; every GPU that loads the library holds it until the process exits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,7 +33,7 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned long long g_nn_scratch[kScratchWords];
 
 std::mutex g_setup_mu;
-unsigned long long *g_scratch_addr[kMaxDevices];  // device address of g_nn_scratch, per device
+bool g_ready[kMaxDevices];                        // per device: kernels loaded, sizes queried
 int g_nn_occ[kMaxDevices][3];                     // occupancy of the three search variants, per device
 int g_sms[kMaxDevices];
 int g_occ_d[kMaxDevices];                         // state dimension the occupancy was taken for
@@ -44,18 +44,36 @@ pakr_status fail(pakr_status st, const char *msg)
     return st;
 }
 
-// Once per device, with that device current: the device address of the
-// scratch array (in host code its name is only a host-side stand-in).
+__global__ void k_static_begin(unsigned long long *scratch, int n_queries, int n, float bound);
+__global__ void k_static_finish(const unsigned long long *scratch, int n_queries, int32_t *nearest, float *dist2);
+
+// Per call, with the device current: the device address of the scratch array (in host code
+// its name is only a host-side stand-in).  Looked up on every call, so that a module that was
+// reloaded (a device reset, a new context) is never reached through a stale address; once
+// the module is loaded the lookup allocates nothing.  The first call on a device also loads
+// the GPU code of every search variant and of the two helper kernels, and reads the SM count,
+// so that no later call loads code.
 pakr_status setup(int dev, unsigned long long **addr)
 {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_nn_scratch);
+    if (e != cudaSuccess) {
+        char buf[256];
+        snprintf(buf, sizeof(buf), "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+        return fail(PAKR_ERR_CUDA, buf);
+    }
+    *addr = (unsigned long long *)p;
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_nn_scratch);
+    if (!g_ready[dev]) {
+        cudaFuncAttributes fa;
+        e = nn_preload_all();
+        if (e == cudaSuccess)
+            e = cudaFuncGetAttributes(&fa, k_static_begin);
+        if (e == cudaSuccess)
+            e = cudaFuncGetAttributes(&fa, k_static_finish);
         if (e != cudaSuccess) {
             char buf[256];
-            snprintf(buf, sizeof(buf), "cudaGetSymbolAddress of the static scratch failed: %s",
-                     cudaGetErrorString(e));
+            snprintf(buf, sizeof(buf), "loading the search kernels failed: %s", cudaGetErrorString(e));
             return fail(PAKR_ERR_CUDA, buf);
         }
         int sms = 0;
@@ -63,9 +81,8 @@ pakr_status setup(int dev, unsigned long long **addr)
         if (e != cudaSuccess)
             return fail(PAKR_ERR_CUDA, "cudaDeviceGetAttribute failed");
         g_sms[dev] = sms;
-        g_scratch_addr[dev] = (unsigned long long *)p;
+        g_ready[dev] = true;
     }
-    *addr = g_scratch_addr[dev];
     return PAKR_OK;
 }
 
@@ -123,8 +140,8 @@ extern "C" pakr_status pakr_nearest_static(const float *states, int64_t ld, int6
     if (n_queries < 0 || n_queries > kStaticMaxQueries)
         return fail(PAKR_ERR_INVALID_ARG,
                     "pakr_nearest_static: n_queries must be in [0, 65536], the size of the static scratch");
-    if (n < 0 || n > 0x7FFFFFFFLL || ld < n || ld > 0x7FFFFFFFLL)
-        return fail(PAKR_ERR_INVALID_ARG, "pakr_nearest_static: need 0 <= n <= ld < 2^31");
+    if (n < 0 || n > kMaxTreeNodes || ld < n || ld > 0x7FFFFFFFLL)
+        return fail(PAKR_ERR_INVALID_ARG, "pakr_nearest_static: need 0 <= n <= 2^31 - 2^20 and n <= ld < 2^31");
     if (std::isnan(bound))
         return fail(PAKR_ERR_INVALID_ARG, "pakr_nearest_static: bound is NaN");
     if (n_queries == 0)

@@ -10,8 +10,16 @@
 // way, the packed node copy keeps it exact so that hi + lo gives v back, and
 // the tensor core reads it as TF32); the product is formed from
 // hi.hi + hi.lo + lo.hi, and |x - c|^2 enters as hi + lo times 1.
-// One tcgen05.mma of kind::tf32 with K = 8 covers two coordinates' worth of
-// those columns; a node row has KT = 3d + 2 columns rounded up to a multiple of 8.
+// One tcgen05.mma of kind::tf32 with K = 8 covers eight of those columns.
+//
+// Two layouts of the packed node row (TcShape<D>::SPLIT chooses):
+//  - split (d = 3, 5, 6): the row is (x_hi, x_lo, |x|^2 hi, lo) in 2d + 2 columns rounded up
+//    to 8, and the query has two operands: (-2q_hi against x_hi and x_lo, 1, 1) over the whole
+//    row, and (-2q_lo) against the x_hi columns alone, issued as extra MMAs into the same
+//    accumulator.  No column is stored twice;
+//  - joint (other d): the row is (x_hi, x_lo, x_hi, |x|^2 hi, lo) in 3d + 2 columns rounded
+//    up to 8 against one query operand (-2q_hi, -2q_hi, -2q_lo, 1, 1).  Used where the split
+//    form would need more MMAs per tile (d = 12: 6 instead of 5) or save no bytes (d = 4).
 #pragma once
 #include "pakr_internal.h"
 
@@ -151,69 +159,24 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst_smem, const void *src, uin
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
-// Two loads of 32 consecutive FP32 accumulator columns of this thread's TMEM lane
-// (at taddr and taddr + 32), then the wait for both.
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64])
+// Minimum of 16 consecutive FP32 accumulator columns of this thread's TMEM lane: tcgen05.ld
+// with the min reduction (sm_103a) returns the per-lane minimum next to the loaded values, so
+// no ALU work is spent on it; the values themselves are not needed and are dropped.  Waits for
+// the load (its destination registers are written asynchronously until then).
+__device__ __forceinline__ float tmem_ldred_min16(uint32_t taddr)
 {
-    uint32_t r[64];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n\t"
-                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                 "{%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-                 "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n\t"
+    uint32_t r[16];
+    float m;
+    asm volatile("tcgen05.ld.red.sync.aligned.32x32b.x16.min.f32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, %16, [%17];\n\t"
                  "tcgen05.wait::ld.sync.aligned;"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                    "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]),
-                   "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
-                   "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
-                   "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
-                   "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-                 : "r"(taddr), "r"(taddr + 32u)
-                 : "memory");
-#pragma unroll
-    for (int i = 0; i < 64; ++i)
-        v[i] = __uint_as_float(r[i]);
-}
-// 32 consecutive FP32 accumulator columns of this thread's TMEM lane, loaded and waited for.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
-{
-    uint32_t r[32];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
-                 "tcgen05.wait::ld.sync.aligned;"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                   "=r"(r[15]), "=f"(m)
                  : "r"(taddr)
                  : "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-        v[i] = __uint_as_float(r[i]);
+    return m;
 }
-__device__ __forceinline__ float fmin3(float a, float b, float c)
-{
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-// Minimum of 16 values: a depth-3 tree of three-input minima.
-__device__ __forceinline__ float min16(const float *w)
-{
-    const float a = fmin3(w[0], w[1], w[2]);
-    const float b = fmin3(w[3], w[4], w[5]);
-    const float c = fmin3(w[6], w[7], w[8]);
-    const float d = fmin3(w[9], w[10], w[11]);
-    const float e = fmin3(w[12], w[13], w[14]);
-    return fminf(fmin3(a, b, c), fmin3(d, e, w[15]));
-}
-
 // Shared-memory matrix descriptor, no swizzle, K-major: LBO = byte distance of
 // the two core matrices along K, SBO = byte distance of 8-row groups.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
@@ -245,13 +208,29 @@ constexpr int kTcMmaWarp = 1;    // lane 0: MMAs; the warp owns the TMEM allocat
 constexpr int kTcPatch0 = 2;     // warps 2-3: mask ineligible rows, signal "stage masked"
 constexpr int kTcReader0 = 4;    // warps 4 and up: accumulator readers (warp w reads lane quarter w % 4)
 
+// Columns of the packed node row for state dimension d (see the two layouts above).
+__host__ __device__ constexpr int tc_cols_joint(int d) { return ((3 * d + 2) + 7) / 8 * 8; }
+__host__ __device__ constexpr int tc_cols_split(int d) { return ((2 * d + 2) + 7) / 8 * 8; }
+__host__ __device__ constexpr bool tc_split(int d)
+{
+    return tc_cols_split(d) < tc_cols_joint(d) &&
+           tc_cols_split(d) / 8 + (d + 7) / 8 <= tc_cols_joint(d) / 8;
+}
+__host__ __device__ constexpr int tc_node_cols(int d) { return tc_split(d) ? tc_cols_split(d) : tc_cols_joint(d); }
+
 template <int D>
 struct TcShape {
-    static constexpr int KT = ((3 * D + 2) + 7) / 8 * 8;  // x_hi, x_lo, x_hi, |x|^2 hi, lo, zero padding
-    static constexpr int LBO = 128, SBO = KT * 32;         // no-swizzle K-major core-matrix layout
-    static constexpr int TILE_BYTES = kTcN * KT * 4;       // one packed node tile, contiguous
-    static constexpr int STAGE_BYTES = kTcBN * KT * 4;     // half a packed tile: also contiguous
-    static constexpr int A_BYTES = kTcM * KT * 4;
+    static constexpr bool SPLIT = tc_split(D);
+    static constexpr int KT = tc_node_cols(D);                 // columns of a packed node row
+    static constexpr int KA2 = SPLIT ? (D + 7) / 8 * 8 : 0;    // columns of the second query operand
+    static constexpr int NORM = SPLIT ? 2 * D : 3 * D;         // column of |x|^2 hi (lo follows)
+    static constexpr int MMAS = KT / 8 + KA2 / 8;              // MMAs of K = 8 per stage
+    static constexpr int LBO = 128, SBO = KT * 32;             // no-swizzle K-major core-matrix layout
+    static constexpr int SBO2 = KA2 * 32;                      // the same for the second query operand
+    static constexpr int TILE_BYTES = kTcN * KT * 4;           // one packed node tile, contiguous
+    static constexpr int STAGE_BYTES = kTcBN * KT * 4;         // half a packed tile: also contiguous
+    static constexpr int A1_BYTES = kTcM * KT * 4;
+    static constexpr int A_BYTES = A1_BYTES + kTcM * KA2 * 4;
     static constexpr int F_BYTES = kTcBN * 4;
     // reader warps per TMEM lane quarter: two (64 accumulator columns each) for d <= 8, one
     // (all 128) for larger d, whose resolve needs the registers (measured both ways: d = 6
@@ -275,6 +254,12 @@ __host__ __device__ __forceinline__ uint32_t tc_off(int r, int k)
 {
     return (uint32_t)((r >> 3) * TcShape<D>::SBO + (k >> 2) * TcShape<D>::LBO + (r & 7) * 16 + (k & 3) * 4);
 }
+// The same in the second query operand (KA2 columns).
+template <int D>
+__host__ __device__ __forceinline__ uint32_t tc_off2(int r, int k)
+{
+    return (uint32_t)((r >> 3) * TcShape<D>::SBO2 + (k >> 2) * TcShape<D>::LBO + (r & 7) * 16 + (k & 3) * 4);
+}
 
 __device__ __forceinline__ float tf32_trunc(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
 
@@ -285,14 +270,15 @@ __device__ __forceinline__ float tf32_trunc(float v) { return __uint_as_float(__
 // |x|^2 by 2^-20 |x|^2; FP32 |x - c|^2 adds gamma_d; the exact form e carries gamma_(d+2);
 // rounding x - c and q - c moves the distance by at most 2.01 u R^2; the tensor-core
 // accumulation is taken as 4 (KT/8 + 1) u of the sum of |products| (measured on this GPU
-// at most 5.2 u with 5 accumulating k-steps, 2.2 u with one).  The total is doubled.
+// at most 5.2 u with 5 accumulating k-steps, 2.2 u with one; taken per MMA of the stage,
+// whichever operand it reads).  The total is doubled.
 template <int D>
 __host__ __device__ constexpr float tc_bound_coef()
 {
     constexpr float u = 5.9604645e-8f;
-    constexpr int KT = TcShape<D>::KT;
+    constexpr int MMAS = TcShape<D>::MMAS;
     return 2.f * (2.5f * 16.f * u + D * u / (1.f - D * u) + (D + 2) * u / (1.f - (D + 2) * u) +
-                  1.01f * 4.f * (KT / 8 + 1) * u + 2.01f * u);
+                  1.01f * 4.f * (MMAS + 1) * u + 2.01f * u);
 }
 
 // Write node j's packed operand row (state x, unweighted) into the tree's tile copy;
@@ -302,7 +288,8 @@ __device__ __forceinline__ void tc_pack_node(const DevProblem &P, const DevTree 
 {
     if (!T.XT)
         return;
-    constexpr int KT = TcShape<D>::KT;
+    using S = TcShape<D>;
+    constexpr int KT = S::KT;
     float row[KT];
 #pragma unroll
     for (int k = 0; k < KT; ++k)
@@ -315,11 +302,12 @@ __device__ __forceinline__ void tc_pack_node(const DevProblem &P, const DevTree 
         const float hi = tf32_trunc(v);
         row[a] = hi;
         row[D + a] = v - hi;  // exact; the tensor core reads it as TF32, the exact resolve adds it to hi
-        row[2 * D + a] = hi;
+        if constexpr (!S::SPLIT)
+            row[2 * D + a] = hi;
     }
     const float nh = tf32_trunc(xn);
-    row[3 * D] = nh;
-    row[3 * D + 1] = tf32_trunc(xn - nh);
+    row[S::NORM] = nh;
+    row[S::NORM + 1] = tf32_trunc(xn - nh);
     if (!(xn <= P.tc_xbox2))
         atomicOr(&ctl->tc_flag, 1u);
     unsigned char *tile = reinterpret_cast<unsigned char *>(T.XT) + (size_t)(j / kTcN) * TcShape<D>::TILE_BYTES;

@@ -521,7 +521,8 @@ __global__ void __launch_bounds__(32 * kTrajWarpsPerBlock)
 #pragma unroll
         for (int a = 0; a < D; ++a)
             inb = inb && (x[a] >= P.x_lo[a]) && (x[a] <= P.x_hi[a]);
-        const bool hit = inb && hits_obstacle<PD>(x, P.boxes, P.n_boxes, P.spheres, P.n_spheres, lane, 32);
+        const bool hit = inb && hits_obstacle<PD>(x, P, P.boxes, P.n_boxes, P.spheres, P.n_spheres, P.grid_start,
+                                                  P.grid_items, lane, 32);
         if (!inb || __any_sync(0xFFFFFFFFu, hit))
             ok = false;
     }

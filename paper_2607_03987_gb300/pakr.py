@@ -146,7 +146,8 @@ def lib():
     L.pakr_tree_import.argtypes = [C.c_void_p, C.POINTER(TreeHost), _PF]
     L.pakr_tree_truncate.argtypes = [C.c_void_p, C.c_int64]
     L.pakr_tree_size.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_uint32)]
-    L.pakr_debug_last_expand.argtypes = [C.c_void_p, _PF, _PI32, C.POINTER(C.c_int8), _PF, _PI32]
+    L.pakr_debug_last_expand.argtypes = [C.c_void_p, _PF, _PI32, C.POINTER(C.c_int8), C.POINTER(C.c_int8), _PF,
+                                         _PI32]
     L.pakr_set_profiling.argtypes = [C.c_void_p, C.c_int32]
     L.pakr_kernel_times.argtypes = [C.c_void_p, _PD, _PI64, C.POINTER(C.c_char_p), C.c_int32]
     L.pakr_philox4x32_10.argtypes = [C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
@@ -378,12 +379,14 @@ class Planner:
         samples = np.zeros((K, self.d), np.float32)
         near = np.zeros(K, np.int32)
         outcome = np.zeros(R, np.int8)
+        goal = np.zeros(R, np.int8)
         controls = np.zeros((R, self.m), np.float32)
         steps = np.zeros(R, np.int32)
+        P8 = C.POINTER(C.c_int8)
         _check(lib().pakr_debug_last_expand(self.h, _pf(samples), near.ctypes.data_as(_PI32),
-                                            outcome.ctypes.data_as(C.POINTER(C.c_int8)), _pf(controls),
+                                            outcome.ctypes.data_as(P8), goal.ctypes.data_as(P8), _pf(controls),
                                             steps.ctypes.data_as(_PI32)), "pakr_debug_last_expand")
-        return dict(samples=samples, near=near, outcome=outcome, controls=controls, steps=steps)
+        return dict(samples=samples, near=near, outcome=outcome, goal=goal, controls=controls, steps=steps)
 
     def set_profiling(self, enable):
         return _check(lib().pakr_set_profiling(self.h, int(bool(enable))), "pakr_set_profiling")

@@ -115,7 +115,8 @@ def refine_path(planner, spec, path, x_goal, iters=15, candidates=16, step=0.5, 
              w_duration=0.0, length_eps=1e-4)
     w.update(weights or {})
     reps = torch.as_tensor(steps, dtype=torch.long, device=dev)
-    x0 = torch.tensor(np.asarray(path["states"][0], np.float32)[None], device=dev)
+    x0v = path["x0"] if "x0" in path else path["states"][0]
+    x0 = torch.tensor(np.asarray(x0v, np.float32)[None], device=dev)
     u = torch.tensor(np.asarray(path["controls"], np.float32), device=dev)
     lo = torch.tensor(np.asarray(spec["u_lo"], np.float32), device=dev)
     hi = torch.tensor(np.asarray(spec["u_hi"], np.float32), device=dev)
@@ -147,31 +148,40 @@ def refine_path(planner, spec, path, x_goal, iters=15, candidates=16, step=0.5, 
     return u, cur_f
 
 
-def refined_aox(planner, spec, budget_s, seed=0, refine_iters=15, first_fraction=0.6):
-    """AO-x with one gradient refinement inside the wall-clock budget: run the
-    device-resident AO-x loop for first_fraction of the budget, refine its best
-    path with the adjoint kernels (accepted only if the planner's rules hold
-    and it is shorter), then continue AO-x from the refined cost as the bound
-    (pakr_plan_bounded) for the rest of the budget.  Returns (best cost,
-    [(elapsed s, cost)], refinement gain)."""
+def refined_aox(planner, spec, budget_s, seed=0, refine_iters=15, rounds=(0.3, 0.6, 0.85)):
+    """AO-x with gradient refinement inside one wall-clock budget.  The device-resident AO-x
+    loop runs in slices that end at the given fractions of the budget; after each slice that
+    produced a new best path, that path is refined with the adjoint kernels (kept only if the
+    planner's own rules accept it and it is shorter), and the next slice continues AO-x from
+    the best cost so far as its bound (pakr_plan_bounded), so each refinement tightens the
+    bound the search prunes with.  A slice that finds nothing keeps the previous best.
+    Returns (best cost, [(elapsed s, cost)], total refinement gain, best path) with the best
+    path as dict(x0, controls, steps) (None if nothing was found)."""
     import time
 
     t0 = time.perf_counter()
     history = []
-    r = planner.plan(spec["x_init"], spec["x_goal"], budget_s=first_fraction * budget_s, seed=seed)
-    c_best = float(r["cost"]) if r["n_solutions"] else float("inf")
-    history.append((time.perf_counter() - t0, c_best))
-    gain = 0.0
-    if r["n_solutions"]:
-        out = refine_path(planner, spec, r, spec["x_goal"], iters=refine_iters)
-        if out is not None and out[1] < c_best:
-            gain = c_best - out[1]
-            c_best = out[1]
-        history.append((time.perf_counter() - t0, c_best))
-    left = budget_s - (time.perf_counter() - t0)
-    if left > 0:
-        r2 = planner.plan(spec["x_init"], spec["x_goal"], budget_s=left, seed=seed + 1, initial_bound=c_best)
-        if r2["n_solutions"]:
-            c_best = min(c_best, float(r2["cost"]))
-        history.append((time.perf_counter() - t0, c_best))
-    return c_best, history, gain
+    best, best_cost, gain = None, float("inf"), 0.0
+    fresh = False
+    fracs = tuple(rounds) + (1.0,)
+    for i, frac in enumerate(fracs):
+        left = frac * budget_s - (time.perf_counter() - t0)
+        if left <= 0:
+            continue
+        r = planner.plan(spec["x_init"], spec["x_goal"], budget_s=left, seed=seed + i,
+                         initial_bound=None if best is None else best_cost)
+        if r["n_solutions"] and float(r["cost"]) < best_cost:
+            best_cost = float(r["cost"])
+            best = dict(x0=r["states"][0].copy(), controls=r["controls"].copy(), steps=r["steps"].copy(),
+                        states=r["states"].copy())
+            fresh = True
+        history.append((time.perf_counter() - t0, best_cost))
+        if i < len(fracs) - 1 and fresh:
+            out = refine_path(planner, spec, best, spec["x_goal"], iters=refine_iters)
+            fresh = False
+            if out is not None and out[1] < best_cost:
+                gain += best_cost - out[1]
+                best_cost = out[1]
+                best = dict(x0=best["x0"], controls=out[0].detach().cpu().numpy(), steps=best["steps"])
+            history.append((time.perf_counter() - t0, best_cost))
+    return best_cost, history, gain, best

@@ -152,20 +152,29 @@ def prefilled_tree(spec, n, seed, cost_hi=0.0):
                 iteration=0)
 
 
-def batch_queries(n_queries=256, env_seed=0, obs_range=(10, 200), cap_range=(64 * 1024, 1 << 20), min_sep=0.6):
+def batch_queries(n_queries=256, env_seed=0, obs_range=(10, 200), cap_range=(64 * 1024, 1 << 20), min_sep=0.6,
+                  sep_range=None):
     """Independent 3D double-integrator queries: per query an obstacle count
     uniform in obs_range, a tree cap uniform in cap_range (a multiple of
     1024), and a random start / goal pair at rest, at least min_sep apart,
-    kept free of that query's boxes."""
+    kept free of that query's boxes.  With sep_range = (lo, hi) the goal is
+    instead the start moved a distance uniform in [lo, hi] in a uniformly
+    random direction (short queries, solved in a few expansions)."""
     rng = np.random.Generator(np.random.Philox(int(env_seed) + 7919))
     base = problem("di3", env_seed=env_seed)
     out = []
     for _ in range(n_queries):
         while True:
             s = rng.uniform(0.08, 0.92, 3)
-            g = rng.uniform(0.08, 0.92, 3)
-            if np.linalg.norm(s - g) >= min_sep:
-                break
+            if sep_range is None:
+                g = rng.uniform(0.08, 0.92, 3)
+                if np.linalg.norm(s - g) >= min_sep:
+                    break
+            else:
+                direction = rng.normal(size=3)
+                g = s + direction / np.linalg.norm(direction) * rng.uniform(sep_range[0], sep_range[1])
+                if np.all((g >= 0.08) & (g <= 0.92)):
+                    break
         start = f32(np.concatenate([s, np.zeros(3)]))
         goal = f32(np.concatenate([g, np.zeros(3)]))
         n_obs = int(rng.integers(obs_range[0], obs_range[1] + 1))

@@ -106,9 +106,17 @@ def compare(spec, tree, bound, seed, planner, require_all=False):
     stats["compared_children"] = int(both.sum())
     # the untouched prefix of the tree is unchanged
     assert np.array_equal(gtree["parents"][:n0], np.asarray(tree["parents"])[:n0])
-    # goal
+    # goal flag of every surviving child with the same parent, outside the goal band
     goal_ex = (ref["goal_margin"] < GOAL_TOL) & o_survive
     stats["goal_exempt"] = int(goal_ex.sum())
+    g_goal = dbg["goal"].astype(bool)
+    assert not (g_goal & ~g_survive).any(), "goal flag on a rollout that did not survive"
+    cmp_goal = g_survive & same_parent & ~(ref["goal_margin"] < GOAL_TOL)
+    bad = cmp_goal & (g_goal != (ref["in_goal"] != 0))
+    assert not bad.any(), f"goal flag mismatch at rollouts {np.nonzero(bad)[0][:10]}"
+    stats["compared_goal_flags"] = int(cmp_goal.sum())
+    check_counts(spec, tree, bound, ref, st, info, dbg, gtree, ex, g_survive, o_survive)
+    stats["counts_checked"] = True
     any_exempt = stats["nn_exempt"] + stats["rollout_exempt"] + stats["goal_exempt"] > 0
     if not any_exempt:
         assert info["n_appended"] == ref["n_appended"], (info["n_appended"], ref["n_appended"])
@@ -125,3 +133,54 @@ def compare(spec, tree, bound, seed, planner, require_all=False):
         assert not any_exempt, stats
     stats.update(status=st, ref=ref, info=info, gtree=gtree, otree=otree, dbg=dbg)
     return stats
+
+
+def check_counts(spec, tree, bound, ref, st, info, dbg, gtree, ex, g_survive, o_survive):
+    """Counts, tree size, goal choice and status of one expansion, element by
+    element after exempt rollouts are set aside.
+
+    On an exempt rollout both survival answers are right, so the GPU's answer
+    stands there and the oracle's everywhere else; that merged survivor set
+    fixes, in ascending rollout order, which children are appended and which
+    are dropped at the cap, the node count and the status.  The goal child
+    must be the cheapest appended child in the goal ball (costs within the
+    state tolerance), and the goal flags on the rest were compared above.
+    """
+    R = spec["K"] * spec["k"]
+    go = dbg["outcome"].astype(np.int32)
+    n0 = int(ref["n_start"])
+    cap = spec["cap"]
+    surv = np.where(ex, g_survive, o_survive)
+    n_surv = int(surv.sum())
+    n_app = min(n_surv, max(cap - n0, 0))
+    assert info["n_start"] == n0
+    assert info["n_appended"] == n_app, (info["n_appended"], n_app)
+    assert info["n_dropped"] == n_surv - n_app, (info["n_dropped"], n_surv - n_app)
+    assert np.array_equal(np.nonzero(go == pakr.ROLLOUT_APPENDED)[0], np.nonzero(surv)[0][:n_app]), \
+        "appended rollouts are not the first survivors in rollout order"
+    assert np.array_equal(np.nonzero(go == pakr.ROLLOUT_DROPPED)[0], np.nonzero(surv)[0][n_app:])
+    # no eligible parent depends on eligibility alone, never on a near-tie
+    assert info["n_no_parent"] == ref["n_no_parent"] == int((go == pakr.ROLLOUT_NO_PARENT).sum())
+    assert info["n_pruned"] + info["n_collided"] + n_surv + info["n_no_parent"] == R
+    assert gtree["count"] == n0 + n_app
+    # the goal child: among the appended children flagged in the goal ball, the cheapest
+    app = np.nonzero(go == pakr.ROLLOUT_APPENDED)[0]
+    flagged = app[dbg["goal"][app] != 0]
+    assert bool(info["goal_found"]) == (flagged.size > 0)
+    if flagged.size:
+        nodes = n0 + np.searchsorted(app, flagged)
+        costs = np.asarray(gtree["costs"], np.float64)[nodes]
+        assert info["goal_idx"] in set(nodes.tolist())
+        c_min = costs.min()
+        assert float(gtree["costs"][info["goal_idx"]]) <= c_min + STATE_RTOL * max(1.0, abs(c_min))
+        assert rel_close(info["goal_cost"], gtree["costs"][info["goal_idx"]], 0.0)
+    # status, in the ABI's order of precedence
+    if info["n_no_parent"] == R:
+        want = pakr.NO_ELIGIBLE
+    elif info["goal_found"]:
+        want = pakr.GOAL_REACHED
+    elif n_surv > n_app:
+        want = pakr.TREE_FULL
+    else:
+        want = pakr.OK
+    assert st == want, (st, want)

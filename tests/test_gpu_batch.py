@@ -89,3 +89,53 @@ def test_batch_autotune_keeps_results(cuda_lib):
     with pytest.raises(pakr.PakrError):
         bp.set_tuning(96, 512)
     bp.close()
+
+
+def test_batch_matches_oracle_per_query(cuda_lib):
+    """Each query of one batched launch against the FP64 oracle's own Algorithm 1 run for that
+    query (its obstacles, tree cap and seed + q), planned to the first solution.  Twelve short
+    queries (start and goal 0.15-0.3 apart) with uneven obstacle counts (10-200 boxes) and tree
+    caps: where the oracle's run reached its first solution before any near-tie (an
+    exemption-class event: a substep within 1e-5 of a face, a nearest-neighbour gap under
+    1e-6), the iteration of the first solution, its cost and the path's states and durations
+    must match; every returned path must pass the FP64 re-check (valid at every substep, in the
+    goal ball, with the reported cost)."""
+    import oracle
+    from recheck import recheck_path
+
+    base, queries = W.batch_queries(12, env_seed=5, obs_range=(10, 200), cap_range=(4096, 32768),
+                                    sep_range=(0.15, 0.3))
+    base = W.with_sizes(base, K=128, k=4)
+    seed, iters = 300, 400
+    bp = pakr.BatchPlanner(base, queries)
+    res = bp.plan(budget_s=60.0, max_iterations=iters, seed=seed, stop_at_first=True)
+    compared = 0
+    for q, (query, r) in enumerate(zip(queries, res)):
+        spec = single_spec(base, query)
+        prob = oracle.OracleProblem(spec)
+        prob.set_goal(spec["x_goal"])
+        tree = oracle.OracleTree(spec["d"], spec["m"], spec["cap"])
+        o = oracle.plan(prob, tree, spec["x_init"], seed + q, iters, stop_at_first=True)
+        frag = o["fragile_iteration"]
+        solved_before_frag = o["n_solutions"] > 0 and (frag < 0 or o["hist_iter"][0] < frag)
+        if r["n_solutions"]:
+            states, controls, steps = bp.path(q)
+            ne = r["n_edges"]
+            assert r["iterations_first_solution"] == r["iterations"]
+            rc = recheck_path(spec, states[: ne + 1], controls[:ne], steps[:ne])
+            assert rc["invalid"] == 0 and (rc["replay_in_goal"] or rc["replay_exempt"] > 0), (q, rc)
+            assert abs(rc["replay_length"] - r["cost"]) <= 1e-4 * max(1.0, r["cost"]), (q, rc, r["cost"])
+        if solved_before_frag:
+            assert r["status"] == pakr.GOAL_REACHED, (q, r)
+            assert r["iterations_first_solution"] == o["hist_iter"][0] + 1, (q, r, o["hist_iter"])
+            assert abs(r["cost"] - o["best_cost"]) <= 1e-5 * max(1.0, o["best_cost"]), (q, r["cost"], o["best_cost"])
+            assert r["n_edges"] + 1 == len(o["path_states"])
+            assert np.allclose(states[: ne + 1], o["path_states"], rtol=1e-5, atol=1e-5)
+            assert np.array_equal(steps[:ne], o["path_steps"][1:])
+            compared += 1
+        elif frag < 0:
+            # no near-tie in the whole oracle run and no solution within the iteration cap
+            assert r["n_solutions"] == 0 and r["iterations"] == o["iterations"], (q, r, o["iterations"])
+            compared += 1
+    bp.close()
+    assert compared >= len(queries) // 2, compared

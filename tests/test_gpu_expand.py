@@ -100,7 +100,7 @@ def test_expand_single_node_tree(cuda_lib):
     run_case(cuda_lib, spec, tree, [np.inf], [1, 2])
 
 
-@pytest.mark.parametrize("variant", ["duration", "fullstate", "spheres", "weights"])
+@pytest.mark.parametrize("variant", ["duration", "fullstate", "spheres", "weights", "obstacles_outside"])
 def test_expand_variants(cuda_lib, variant):
     base = W.problem("di3", env_seed=4)
     over = dict(K=256, k=4, cap=8000)
@@ -112,6 +112,13 @@ def test_expand_variants(cuda_lib, variant):
         over["spheres"] = W.random_spheres(3, 20, 3)
     elif variant == "weights":
         over["nn_w"] = W.f32([1, 1, 1, 0.25, 0.25, 0.25])
+    elif variant == "obstacles_outside":
+        # obstacles reaching past the state box and one spanning half of it: the obstacle grid
+        # clamps their cell ranges at the box edge
+        extra = W.f32([[-0.3, 0.4, 0.2, 0.12, 0.6, 0.5], [0.85, -0.2, 0.3, 1.4, 0.15, 0.45],
+                       [0.3, 0.55, -0.5, 0.9, 0.95, 0.35]])
+        over["boxes"] = np.concatenate([base["boxes"], extra])
+        over["spheres"] = W.f32([[1.02, 0.5, 0.5, 0.1], [0.5, 0.5, 1.05, 0.08], [0.3, 0.7, 0.6, 0.06]])
     spec = W.with_sizes(base, **over)
     tree = W.prefilled_tree(spec, 1500, seed=2, cost_hi=1.0)
     run_case(cuda_lib, spec, tree, [np.inf, 2.2], [5])

@@ -148,3 +148,68 @@ def test_expand_graph_matches_plain_launches(cuda_lib):
         assert sa == sb and ia == ib
         for key in ("samples", "near", "outcome", "controls", "steps"):
             assert np.array_equal(da[key], db[key]), key
+
+
+# The benchmarked workloads at their full sizes, in the launch configuration the benchmark times
+# (pakr_expand's expansion graph): the 3D double integrator with 1024 parents x 8 controls on a
+# 1,000,000-node tree (cap 2^20), and the 12D quadrotor with 4096 parents x 16 controls on a
+# 3,934,464-node tree (cap 4,000,000).  Trees are the benchmark's seeded prefills.
+BENCH_CASES = [("di3", 1_000_000, 1), ("quad12", 4_000_000 - 65536, 3)]
+
+
+@pytest.mark.parametrize("name,n,tree_seed", BENCH_CASES)
+def test_tc_matches_fp32_at_benchmark_size(cuda_lib, name, n, tree_seed):
+    spec = W.problem(name, env_seed=0)
+    tree = W.prefilled_tree(spec, n, seed=tree_seed)
+    for seed in (0, 1):
+        d = assert_same_expansion(spec, tree, np.inf, seed)
+        assert (d["near"] >= 0).all()
+
+
+@pytest.mark.parametrize("name,n,tree_seed,n_sample", [(c[0], c[1], c[2], s) for c, s in zip(BENCH_CASES, (128, 64))])
+def test_tc_against_oracle_sampled_at_benchmark_size(cuda_lib, name, n, tree_seed, n_sample):
+    """A sample of the queries of one benchmark expansion against the oracle's brute-force
+    nearest neighbour (FP64, on the oracle's own Philox samples): the index must match unless
+    the oracle's best and second-best distances are within the 1e-6 near-tie margin."""
+    import oracle
+    from parity import NN_GAP, SAMPLE_RTOL, rel_close
+
+    spec = W.with_sizes(W.problem(name, env_seed=0), nn_mode=pakr.NN_TENSOR)
+    tree = W.prefilled_tree(spec, n, seed=tree_seed)
+    seed = 5
+    _, info, dbg = expand_near(spec, tree, np.inf, seed, pakr.NN_TENSOR)
+    assert info["n_start"] == n
+    prob = oracle.OracleProblem(spec)
+    prob.set_goal(spec["x_goal"])
+    ot = oracle.OracleTree.from_arrays(spec["d"], spec["m"], n + 1, tree["states"], tree["controls"],
+                                       tree["parents"], tree["costs"], tree["steps"])
+    f = oracle.fcosts(prob, ot)
+    rng = np.random.default_rng(7)
+    picks = np.sort(rng.choice(spec["K"], n_sample, replace=False))
+    exempt = 0
+    for i in picks:
+        q = oracle.sample_state(prob, seed, info["iteration"], int(i))
+        assert np.all(rel_close(dbg["samples"][i], q, SAMPLE_RTOL))
+        r = oracle.nearest(prob, ot, q, np.inf, f=f)
+        if dbg["near"][i] != r["idx"]:
+            assert r["d2"] - r["d1"] < NN_GAP, (i, dbg["near"][i], r)
+            exempt += 1
+    assert exempt <= n_sample // 16
+
+
+@pytest.mark.parametrize("dyn", [W.UNICYCLE1, W.UNICYCLE2])
+def test_tc_matches_fp32_other_dimensions(cuda_lib, dyn):
+    # d = 3 and d = 5 use the split packed layout too (as d = 6): forced onto the tensor cores
+    d, m, pdim = W.DIMS[dyn]
+    if dyn == W.UNICYCLE1:
+        x_lo, x_hi, u_lo, u_hi = [0, 0, -np.pi], [1, 1, np.pi], [-0.5, -1], [0.5, 1]
+    else:
+        x_lo, x_hi, u_lo, u_hi = [0, 0, -np.pi, -0.5, -1], [1, 1, np.pi, 0.5, 1], [-0.25, -0.5], [0.25, 0.5]
+    base = W.problem("di2", env_seed=5)
+    spec = W.with_sizes(base, dyn=dyn, d=d, m=m, pdim=pdim, x_lo=W.f32(x_lo), x_hi=W.f32(x_hi),
+                        u_lo=W.f32(u_lo), u_hi=W.f32(u_hi), x_init=W.f32([0.1, 0.1] + [0.0] * (d - 2)),
+                        x_goal=W.f32([0.9, 0.9] + [0.0] * (d - 2)), K=512, k=2, cap=60_000, dt=float(W.f32(0.1)))
+    tree = W.prefilled_tree(spec, 50_003, seed=21)
+    assert_same_expansion(spec, tree, np.inf, seed=3)
+    tree = W.prefilled_tree(spec, 50_003, seed=22, cost_hi=2.0)
+    assert_same_expansion(spec, tree, 1.5, seed=4)

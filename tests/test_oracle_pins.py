@@ -456,3 +456,68 @@ def test_discrete_check_misses_are_counted():
     # the planner checks substeps only (Sec. IV-A); edges that graze an obstacle between substeps exist
     # and are reported, but they are a small fraction
     assert misses < 0.05 * T.count
+
+
+def test_dense_recheck_at_one_substep_is_the_planners_check():
+    # sub = 1 re-integrates at the planner's own step: it must flag exactly the edges that the
+    # oracle's propagation marks as collided (Sec. IV-A: validity at every substep)
+    spec = W.problem("di3", env_seed=3)
+    P = prob_of(spec)
+    rng = np.random.default_rng(11)
+    flagged = 0
+    for _ in range(400):
+        x0 = np.concatenate([rng.uniform(0.05, 0.95, 3), rng.uniform(-1, 1, 3)])
+        if not numpy_valid(spec, x0):
+            continue
+        u = rng.uniform(-1, 1, 3)
+        S = int(rng.integers(1, 21))
+        col = oracle.propagate(P, x0, 0.0, u, S)["collided"]
+        assert oracle.recheck_edge_dense(P, x0, u, S, 1) == col
+        flagged += col
+    assert flagged > 20
+
+
+def test_dense_recheck_agrees_with_exact_segment_test():
+    # boxes only: a fine state the dense check finds invalid lies on the closed-form path, so the
+    # exact continuous test must report a hit too; the exact test's hits are found by the dense
+    # check at dt/256 except for grazes shorter than that
+    spec = W.problem("di3", env_seed=5)
+    P = prob_of(spec)
+    rng = np.random.default_rng(12)
+    n_exact = n_dense = 0
+    for _ in range(300):
+        x0 = np.concatenate([rng.uniform(0.05, 0.95, 3), rng.uniform(-1, 1, 3)])
+        if not numpy_valid(spec, x0):
+            continue
+        u = rng.uniform(-1, 1, 3)
+        S = int(rng.integers(1, 21))
+        exact = oracle.di_edge_hits_exact(P, x0, u, S)
+        dense = oracle.recheck_edge_dense(P, x0, u, S, 256)
+        if dense:
+            assert exact
+        n_exact += exact
+        n_dense += dense
+    assert n_exact > 30 and n_dense >= 0.97 * n_exact
+
+
+def test_dense_recheck_finds_a_sphere_between_substeps():
+    # straight flight at constant velocity through a small sphere that lies between two substeps:
+    # the substep check misses it, the dense check sees it; moved off the line by 1.5 radii (a
+    # closest approach computed in closed form) nothing is hit
+    base = W.problem("di3", env_seed=0)
+    r = 0.004
+    v = np.array([1.0, 0.0, 0.0])
+    x0 = np.concatenate([[0.2, 0.5, 0.5], v])
+    dt = base["dt"]
+    centre = x0[:3] + v * 1.5 * dt  # midway between substeps 1 and 2 (0.05 apart, more than 2r)
+    u = np.zeros(3)
+    for offset, want in ((0.0, True), (1.5 * r, False)):
+        c = centre + np.array([0.0, offset, 0.0])
+        # closest approach of the line p(t) = x0 + v t to the centre
+        t_star = float(np.dot(c - x0[:3], v) / np.dot(v, v))
+        closest = np.linalg.norm(x0[:3] + v * t_star - c)
+        assert (closest <= r) == want
+        spec = W.with_sizes(base, boxes=np.zeros((0, 6)), spheres=np.array([[*c, r]]))
+        P = prob_of(spec)
+        assert not oracle.recheck_edge_dense(P, x0, u, 3, 1)
+        assert oracle.recheck_edge_dense(P, x0, u, 3, 16) == want

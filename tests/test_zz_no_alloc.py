@@ -1,11 +1,15 @@
 """pakr_nearest_static, the nearest-neighbour entry point that allocates nothing.
 
-Callers that cannot allocate device memory (stream capture, real-time loops,
-plugins confined to another framework's pool) pass their own inputs and
-outputs; the search scratch is a static device array inside the library.  Its
-answers must equal the nearest neighbours pakr_expand chose for the same
-samples on the same tree, on two calls in a row (the second call reuses the
-scratch the first one left behind).  This file is collected last on purpose.
+Callers that cannot allocate device memory (real-time loops that forbid
+allocation after start-up, plugins confined to another framework's memory
+pool) pass their own inputs and outputs; the search scratch is a static device
+array inside the library.  Its answers must equal the nearest neighbours
+pakr_expand chose for the same samples on the same tree, on two calls in a row
+(the second call reuses the scratch the first one left behind), within the
+near-tie margin the other parity tests use: pakr_expand ranks distances on
+coordinates centred on the state box, which round differently, so the two may
+differ only where the FP64 distances of their two choices are within 1e-6.
+This file is collected last on purpose.
 """
 import ctypes as C
 
@@ -14,6 +18,7 @@ import pytest
 
 from paper_2607_03987_gb300 import pakr
 from paper_2607_03987_gb300 import workloads as W
+from parity import NN_GAP
 
 pytestmark = pytest.mark.gpu
 
@@ -45,7 +50,13 @@ def test_nearest_static_matches_expand(cuda_lib):
         assert st == pakr.OK, lib.pakr_last_error()
         torch.cuda.synchronize()
         got = nearest.cpu().numpy()
-        assert np.array_equal(got, dbg["near"]), f"call {call}: {np.nonzero(got != dbg['near'])[0][:10]}"
+        diff_q = np.nonzero(got != dbg["near"])[0]
+        q64 = dbg["samples"].astype(np.float64)
+        for i in diff_q:
+            a = np.linalg.norm(q64[i] - tree["states"][got[i]])
+            b = np.linalg.norm(q64[i] - tree["states"][dbg["near"][i]])
+            assert abs(a - b) < NN_GAP, f"call {call}, query {i}: {got[i]} vs {dbg['near'][i]} ({a} vs {b})"
+        assert len(diff_q) <= K // 100
         # the reported squared distance is the FP32 distance to the chosen node
         diff = dbg["samples"].astype(np.float64) - tree["states"][got]
         want = np.sum(diff * diff, axis=1)
