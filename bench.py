@@ -133,8 +133,9 @@ def measured_peaks():
 # dram__bytes_read.sum + dram__bytes_write.sum of one tensor-core nearest-neighbour launch
 # (k_nn_tc) on the bench workload (n = 1,000,000 nodes, d = 6), from the ncu capture named in
 # NN_DRAM_SOURCE.  None when the kernel has changed since that capture.
-NN_DRAM_BYTES_NCU = None
-NN_DRAM_SOURCE = None
+NN_DRAM_BYTES_NCU = 68.143e6 + 3.242e6
+NN_DRAM_SOURCE = ("profiles/k_nn_tc_di3_n1M.md, current kernel (split packed layout, group minima from "
+                  "tcgen05.ld.red): dram__bytes_read.sum + dram__bytes_write.sum of one launch")
 
 # Nominal dense TF32 / BF16 tensor throughput ratio (1.1 / 2.25 PFLOP/s): the TF32 peak is
 # the measured BF16 GEMM rate times this.
@@ -680,7 +681,14 @@ def main():
                          "kernels inside the expansion graph's conditional nodes)")
     ap.add_argument("--only-expand", action="store_true",
                     help="time the expansion steps only (no e2e, planning metrics or CPU leg)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["di2", "di3", "quad12"],
+                    help="with --only-expand: the workload whose expansions are timed")
+    ap.add_argument("--n-tree", type=int, default=N_PREFILL,
+                    help="with --only-expand: the prefilled tree size")
     args = ap.parse_args()
+    if not args.only_expand and (args.workload != WORKLOAD or args.n_tree != N_PREFILL):
+        ap.error("--workload and --n-tree apply to --only-expand runs; the full line measures "
+                 f"{WORKLOAD} at {N_PREFILL} nodes")
     if args.impl == "reference":
         return run_reference(args)
     assert args.warmup >= 3, "at least 3 warm-up steps"
@@ -699,8 +707,11 @@ def main():
     from paper_2607_03987_gb300 import workloads as W
 
     _build.build()
-    spec = W.problem(WORKLOAD, env_seed=0)
-    tree = W.prefilled_tree(spec, N_PREFILL, seed=1 + rank)
+    n_tree = args.n_tree
+    spec = W.problem(args.workload, env_seed=0)
+    if n_tree + spec["K"] * spec["k"] > spec["cap"]:
+        spec = W.with_sizes(spec, cap=n_tree + spec["K"] * spec["k"])
+    tree = W.prefilled_tree(spec, n_tree, seed=1 + rank)
     stream = torch.cuda.current_stream(dev)
     planner = pakr.Planner(spec, device=dev, stream=stream)
     planner.tree_import(tree, spec["x_goal"])
@@ -713,7 +724,7 @@ def main():
 
     clocks = ClockSampler(dev).start()  # samples span the warm-up and the timed steps
     for w in range(args.warmup):
-        planner.tree_truncate(N_PREFILL)
+        planner.tree_truncate(n_tree)
         one_step(10_000 + w)
     torch.cuda.synchronize(dev)
 
@@ -727,7 +738,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize(dev)
     for s in range(args.steps):
-        planner.tree_truncate(N_PREFILL)
+        planner.tree_truncate(n_tree)
         flush.zero_()
         starts[s].record(stream)
         one_step(s)
@@ -746,7 +757,7 @@ def main():
     planner.set_profiling(True)
     substeps = []
     for s in range(min(args.steps, 300)):
-        planner.tree_truncate(N_PREFILL)
+        planner.tree_truncate(n_tree)
         flush.zero_()
         one_step(20_000 + s)
         if s < 20:
@@ -761,7 +772,8 @@ def main():
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                               "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps,
                               "kernel_ms_per_step": kernel_ms, "gpu_launches": launches,
-                              "config": {"workload": WORKLOAD_DESC}}), flush=True)
+                              "config": {"workload": args.workload, "n_tree": n_tree, "parents": spec["K"],
+                                         "branching": spec["k"]}}), flush=True)
         planner.close()
         if ws > 1:
             dist.destroy_process_group()

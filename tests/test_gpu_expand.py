@@ -174,3 +174,16 @@ def test_consecutive_expansions_match_oracle(cuda_lib):
         assert np.all(np.abs(g["costs"] - o["costs"]) <= 1e-5 * np.maximum(1, np.abs(o["costs"])))
     else:
         pytest.fail(f"free-running trees diverged at iteration {diverged}")
+
+
+@pytest.mark.parametrize("K,k", [(2048, 2), (32, 128)])
+def test_expand_table4_extreme_shapes(cuda_lib, K, k):
+    """The two extreme batch shapes of Table 4 on the 12D quadrotor (batch 4096 rollouts as
+    K = 2048 parents x A = 2 and K = 32 x A = 128), one expansion each from a tree the oracle
+    grew and from a prefilled tree with a finite bound, element by element against the oracle."""
+    spec = W.with_sizes(W.problem("quad12", env_seed=0), K=K, k=k, cap=60000)
+    tree = oracle_grown_tree(W.with_sizes(spec, K=256, k=16), 3, seed=7)
+    stats = run_case(cuda_lib, spec, tree, [np.inf], [31])
+    pre = W.prefilled_tree(spec, 20011, seed=8, cost_hi=2.0)
+    stats += run_case(cuda_lib, spec, pre, [2.2], [32])
+    assert sum(s["compared_rollouts"] for s in stats) > 0.9 * 2 * K * k
