@@ -253,6 +253,26 @@ pakr_status pakr_plan_bounded(pakr_planner *planner, const float *x_init, const 
                               int64_t max_iterations, uint64_t seed, uint32_t flags, float initial_bound,
                               pakr_path *out);
 
+/* Lower the AO-x bound c_best of a pakr_plan / pakr_plan_bounded run that is
+ * in progress on this planner to *cost_dev (device memory, one float read on
+ * the device) if that is smaller: AO-x continued from a cheaper path found
+ * outside the loop, such as a gradient-refined path (the paper has no
+ * counterpart; the loop itself is Algorithm 1).  Only enqueues one small
+ * kernel on cuda_stream (NULL = default stream), which should be another
+ * stream than the planner's, so that it runs while the plan's graph runs; the
+ * loop picks the bound up at its next iteration, and nodes and children that
+ * can no longer beat it are pruned from then on.  This is the one call that
+ * may be made from another host thread while pakr_plan runs on this planner.
+ * The kernel's GPU code is loaded at pakr_create, so the call loads nothing
+ * (a first, lazy load could wait for the running plan); the caller should
+ * likewise allocate cost_dev, and launch once any kernel of its own that
+ * writes it, before the plan starts.  An offer that lands before the plan's first iteration is
+ * overwritten by its start (pass such a bound as initial_bound instead); one that lands
+ * after the plan ended is kept until the next plan starts.  A non-finite or
+ * negative cost is ignored.  pakr_path.cost stays the cost of the run's own
+ * best path.  PAKR_ERR_INVALID_ARG for NULL arguments. */
+pakr_status pakr_plan_offer_bound(pakr_planner *planner, const float *cost_dev, void *cuda_stream);
+
 /* Current node count of the tree (and the expansion counter, if iteration is
  * not NULL).  Synchronises the stream; reads two words, not the tree.
  * PAKR_ERR_INVALID_ARG if planner or count is NULL. */

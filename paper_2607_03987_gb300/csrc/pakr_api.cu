@@ -900,6 +900,9 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
         P.grid_start = (const int *)(b + L.grid_start);
         P.grid_items = (const unsigned short *)(b + L.grid_items);
     }
+    e = preload_offer_bound();
+    if (e != cudaSuccess)
+        return cleanup(fail(PAKR_ERR_CUDA, "loading the bound-offer kernel failed: %s", cudaGetErrorString(e)));
     e = cudaMemset(p->ctl, 0, sizeof(Ctl));
     if (e != cudaSuccess)
         return cleanup(fail(PAKR_ERR_CUDA, "cudaMemset failed: %s", cudaGetErrorString(e)));
@@ -956,9 +959,9 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
     while (lanes < kMaxPropLanes && R * lanes * 2 <= (int64_t)sms * 1536 && lanes * 2 <= std::max(1.0, tests))
         lanes *= 2;
     C.prop_lanes = lanes;
-    // 256-thread blocks (measured: 64-thread blocks, which spread the quadrotor's 65536 rollouts
-    // more evenly over the SMs, were slower, 56.6 vs 51.2 us, as every block stages the obstacles
-    // and the grid)
+    // 256-thread blocks at every lane count (measured at one lane per rollout: 128- and
+    // 64-thread blocks, which spread the rollouts over more SMs, took 22.8 and 27.0 us for di3
+    // and 57.3 and 65.1 us for the quadrotor, against 20.9 and 54.2 us)
     C.prop_threads = kPropThreads;
     const int64_t rollouts_per_block = C.prop_threads / lanes;
     C.prop_blocks = (int)((R + rollouts_per_block - 1) / rollouts_per_block);
@@ -1105,7 +1108,7 @@ pakr_status pakr_plan_bounded(pakr_planner *p, const float *x_init, const float 
     if (st != PAKR_OK)
         return st;
     const Ctl &c = *p->ctl_host;
-    out->cost = c.n_solutions > 0 ? c.c_best : INFINITY;
+    out->cost = c.n_solutions > 0 ? c.sol_best : INFINITY;
     out->n_solutions = c.n_solutions;
     out->n_restarts = c.n_restarts;
     out->iterations = c.iterations_done;
@@ -1157,6 +1160,15 @@ pakr_status pakr_plan_bounded(pakr_planner *p, const float *x_init, const float 
     if (c.plan_status == 3)
         return PAKR_NO_ELIGIBLE;
     return PAKR_BUDGET_EXPIRED;
+}
+
+pakr_status pakr_plan_offer_bound(pakr_planner *p, const float *cost_dev, void *cuda_stream)
+{
+    if (!p || !cost_dev)
+        return fail(PAKR_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard guard(p->device);
+    CUDA_TRY(launch_offer_bound(p->ctl, cost_dev, (cudaStream_t)cuda_stream));
+    return PAKR_OK;
 }
 
 pakr_status pakr_tree_size(pakr_planner *p, int64_t *count, uint32_t *iteration)

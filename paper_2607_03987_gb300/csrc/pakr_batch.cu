@@ -655,7 +655,7 @@ pakr_status pakr_batch_plan(pakr_batch *b, double budget_s, int64_t max_iteratio
         pakr_batch_result &r = results[q];
         memset(&r, 0, sizeof(r));
         r.n_solutions = c.n_solutions;
-        r.cost = c.n_solutions > 0 ? c.c_best : INFINITY;
+        r.cost = c.n_solutions > 0 ? c.sol_best : INFINITY;
         r.n_edges = c.n_solutions > 0 ? (c.path_len > 0 ? c.path_len - 1 : -1) : 0;
         r.iterations = c.iterations_done;
         r.t_first_solution_s = c.t_first_ns == ~0ull ? -1.0 : (double)c.t_first_ns * 1e-9;

@@ -54,6 +54,21 @@ __device__ __forceinline__ float u01(uint32_t w) { return (float)(w >> 8) * (1.0
 
 __device__ __forceinline__ float lerp_box(float lo, float hi, uint32_t w) { return __fmaf_rn(hi - lo, u01(w), lo); }
 
+// Squared distance of the first N coordinates of a and b as a chain of fused multiply-adds
+// (the library compiles without implicit contraction, so it is written out).
+template <int N>
+__device__ __forceinline__ float sq_dist(const float *a, const float *b)
+{
+    const float d0 = a[0] - b[0];
+    float dd = __fmul_rn(d0, d0);
+#pragma unroll
+    for (int k = 1; k < N; ++k) {
+        const float dk = a[k] - b[k];
+        dd = __fmaf_rn(dk, dk, dd);
+    }
+    return dd;
+}
+
 __device__ __forceinline__ unsigned long long globaltimer_ns()
 {
     unsigned long long t;
@@ -223,10 +238,8 @@ __device__ __forceinline__ bool state_valid(const float *x, const DevProblem &P,
     }
     for (int s = 0; s < ns; ++s) {
         const float4 c = spheres[s];
-        float dd = (x[0] - c.x) * (x[0] - c.x) + (x[1] - c.y) * (x[1] - c.y);
-        if (PD > 2)
-            dd += (x[2] - c.z) * (x[2] - c.z);
-        if (dd <= c.w * c.w)
+        const float cc[3] = {c.x, c.y, c.z};
+        if (sq_dist<PD>(x, cc) <= c.w * c.w)
             return false;
     }
     return true;
@@ -238,18 +251,9 @@ __device__ __forceinline__ bool state_valid(const float *x, const DevProblem &P,
 template <int D, int PD>
 __device__ __forceinline__ float heuristic(const float *x, const DevProblem &P, const float *goal)
 {
-    if (P.heuristic == H_FULLSTATE) {
-        float dd = 0.f;
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-            dd += (x[a] - goal[a]) * (x[a] - goal[a]);
-        return sqrtf(dd);
-    }
-    float dd = 0.f;
-#pragma unroll
-    for (int a = 0; a < PD; ++a)
-        dd += (x[a] - goal[a]) * (x[a] - goal[a]);
-    const float h = fmaxf(0.f, sqrtf(dd) - P.goal_r);
+    if (P.heuristic == H_FULLSTATE)
+        return sqrtf(sq_dist<D>(x, goal));
+    const float h = fmaxf(0.f, sqrtf(sq_dist<PD>(x, goal)) - P.goal_r);
     if (P.cost == COST_DURATION)
         return P.h_speed > 0.f ? h / P.h_speed : 0.f;
     return h;
@@ -258,11 +262,7 @@ __device__ __forceinline__ float heuristic(const float *x, const DevProblem &P, 
 template <int PD>
 __device__ __forceinline__ bool in_goal(const float *x, const DevProblem &P, const float *goal)
 {
-    float dd = 0.f;
-#pragma unroll
-    for (int a = 0; a < PD; ++a)
-        dd += (x[a] - goal[a]) * (x[a] - goal[a]);
-    return dd <= P.goal_r * P.goal_r;
+    return sq_dist<PD>(x, goal) <= P.goal_r * P.goal_r;
 }
 
 // ---------------------------------------------------------------------------
@@ -647,10 +647,8 @@ template <int PD>
 __device__ __forceinline__ bool in_sphere(const float *x, const float4 *spheres, int s)
 {
     const float4 c = spheres[s];
-    float dd = (x[0] - c.x) * (x[0] - c.x) + (x[1] - c.y) * (x[1] - c.y);
-    if (PD > 2)
-        dd += (x[2] - c.z) * (x[2] - c.z);
-    return dd <= c.w * c.w;
+    const float cc[3] = {c.x, c.y, c.z};
+    return sq_dist<PD>(x, cc) <= c.w * c.w;
 }
 
 // Obstacle test of position x on this lane's share (first, first + stride, ...) of the
@@ -682,6 +680,26 @@ __device__ __forceinline__ bool hits_obstacle(const float *x, const DevProblem &
     return false;
 }
 
+// Block-wide copy of n elements from global to shared memory with every thread's loads (up to
+// four) issued before its stores, so that a block staging a few KB pays about one memory round
+// trip instead of one per loop pass.
+template <typename T>
+__device__ __forceinline__ void stage_to_shared(T *dst, const T *src, int n)
+{
+    const int nt = blockDim.x;
+    for (int t0 = threadIdx.x; t0 < n; t0 += 4 * nt) {
+        T v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (t0 + k * nt < n)
+                v[k] = src[t0 + k * nt];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (t0 + k * nt < n)
+                dst[t0 + k * nt] = v[k];
+    }
+}
+
 // Rollouts of propagate block vb (blockDim.x / LG rollouts) with the obstacles staged into
 // s_obs (2 n_boxes + n_spheres float4, then the goal, then the obstacle grid's cell offsets and
 // lists).
@@ -695,19 +713,6 @@ __device__ __forceinline__ void propagate_block(const DevProblem &P, Ctl *ctl, c
     float *s_goal = reinterpret_cast<float *>(s_sph + P.n_spheres);
     int *s_gstart = reinterpret_cast<int *>(s_goal + kMaxD);
     unsigned short *s_gitems = reinterpret_cast<unsigned short *>(s_gstart + P.grid_cells + 1);
-    for (int t = threadIdx.x; t < 2 * P.n_boxes; t += blockDim.x)
-        s_box[t] = P.boxes[t];
-    for (int t = threadIdx.x; t < P.n_spheres; t += blockDim.x)
-        s_sph[t] = P.spheres[t];
-    if (threadIdx.x < D)
-        s_goal[threadIdx.x] = ctl->x_goal[threadIdx.x];
-    if (P.grid_g > 0) {
-        for (int t = threadIdx.x; t <= P.grid_cells; t += blockDim.x)
-            s_gstart[t] = P.grid_start[t];
-        for (int t = threadIdx.x; t < P.grid_n_items; t += blockDim.x)
-            s_gitems[t] = P.grid_items[t];
-    }
-    __syncthreads();
 
     const int R = P.K * P.k;
     const int lane = threadIdx.x & 31;
@@ -721,6 +726,8 @@ __device__ __forceinline__ void propagate_block(const DevProblem &P, Ctl *ctl, c
     const bool early = (P.cost == COST_PATH_LENGTH) && (P.heuristic == H_POSITION) &&
                        (bound < __int_as_float(0x7f800000));
 
+    // SampleControls and the parent's state first: their global loads are in flight while the
+    // block stages the obstacles below
     int out = -1;
     bool alive = false;
     float u[M];
@@ -732,7 +739,7 @@ __device__ __forceinline__ void propagate_block(const DevProblem &P, Ctl *ctl, c
         const int j = r - i * P.k;
         const uint32_t it = ctl->iteration;
         const unsigned long long seed = ctl->seed;
-        // SampleControls: words 0..M-1 the control, word M the duration.
+        // words 0..M-1 the control, word M the duration
         constexpr int NB = (M + 1 + 3) / 4;
         uint32_t words[4 * NB];
 #pragma unroll
@@ -766,6 +773,25 @@ __device__ __forceinline__ void propagate_block(const DevProblem &P, Ctl *ctl, c
             }
         }
     }
+    stage_to_shared(s_box, P.boxes, 2 * P.n_boxes);
+    stage_to_shared(s_sph, P.spheres, P.n_spheres);
+    if (threadIdx.x < D)
+        s_goal[threadIdx.x] = ctl->x_goal[threadIdx.x];
+    if (P.grid_g > 0) {
+        stage_to_shared(s_gstart, P.grid_start, P.grid_cells + 1);
+        stage_to_shared(s_gitems, P.grid_items, P.grid_n_items);
+    }
+    // outcome counters: cleared by thread 0 alone, the thread that read them at the end of the
+    // block's previous call (the batched planner calls this body once per work item)
+    __shared__ int s_cnt[4];
+    if (threadIdx.x == 0) {
+        s_cnt[0] = 0;
+        s_cnt[1] = 0;
+        s_cnt[2] = 0;
+        s_cnt[3] = 0;
+    }
+    __syncthreads();
+
     // one lane per rollout: each lane runs its own substeps; with several lanes per rollout
     // every lane of the warp reaches each substep's ballot
     const int s_last = (LG == 1) ? (alive ? S : 0) : __reduce_max_sync(0xFFFFFFFFu, alive ? S : 0);
@@ -778,13 +804,8 @@ __device__ __forceinline__ void propagate_block(const DevProblem &P, Ctl *ctl, c
             for (int a = 0; a < PD; ++a)
                 xp[a] = x[a];
             rk4_step<DYN>(x, u, P.dt, P);
-            if (P.cost == COST_PATH_LENGTH) {
-                float dd = 0.f;
-#pragma unroll
-                for (int a = 0; a < PD; ++a)
-                    dd += (x[a] - xp[a]) * (x[a] - xp[a]);
-                g += sqrtf(dd);
-            }
+            if (P.cost == COST_PATH_LENGTH)
+                g += sqrtf(sq_dist<PD>(x, xp));
             inb = in_state_box<D, PD>(x, P);
         }
         const bool hit = act && inb &&
@@ -824,18 +845,30 @@ __device__ __forceinline__ void propagate_block(const DevProblem &P, Ctl *ctl, c
         W.goal[r] = (out == OUT_APPENDED && in_goal<PD>(x, P, s_goal)) ? 1 : 0;
         W.outcome[r] = (int8_t)out;
     }
-    const int n_cand = __syncthreads_count(leader && out == OUT_APPENDED);
-    const int n_pr = __syncthreads_count(leader && out == OUT_PRUNED);
-    const int n_col = __syncthreads_count(leader && out == OUT_COLLIDED);
-    const int n_np = __syncthreads_count(leader && out == OUT_NO_PARENT);
+    // the four outcome counts of the block: warp ballots into the shared counters, one barrier
+    const unsigned c_app = __ballot_sync(0xFFFFFFFFu, leader && out == OUT_APPENDED);
+    const unsigned c_pr = __ballot_sync(0xFFFFFFFFu, leader && out == OUT_PRUNED);
+    const unsigned c_col = __ballot_sync(0xFFFFFFFFu, leader && out == OUT_COLLIDED);
+    const unsigned c_np = __ballot_sync(0xFFFFFFFFu, leader && out == OUT_NO_PARENT);
+    if (lane == 0) {
+        if (c_app)
+            atomicAdd(&s_cnt[0], __popc(c_app));
+        if (c_pr)
+            atomicAdd(&s_cnt[1], __popc(c_pr));
+        if (c_col)
+            atomicAdd(&s_cnt[2], __popc(c_col));
+        if (c_np)
+            atomicAdd(&s_cnt[3], __popc(c_np));
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        W.block_count[vb] = n_cand;
-        if (n_pr)
-            atomicAdd(&ctl->n_pruned, n_pr);
-        if (n_col)
-            atomicAdd(&ctl->n_collided, n_col);
-        if (n_np)
-            atomicAdd(&ctl->n_no_parent, n_np);
+        W.block_count[vb] = s_cnt[0];
+        if (s_cnt[1])
+            atomicAdd(&ctl->n_pruned, s_cnt[1]);
+        if (s_cnt[2])
+            atomicAdd(&ctl->n_collided, s_cnt[2]);
+        if (s_cnt[3])
+            atomicAdd(&ctl->n_no_parent, s_cnt[3]);
     }
 }
 
@@ -960,7 +993,8 @@ __device__ __forceinline__ void append_block(const DevProblem &P, Ctl *ctl, cons
 // ExtractPath) and the tree restarts from its root; a tree that filled
 // without a solution restarts too; the run stops at the first solution if
 // asked, when no node can beat c_best, or when the device-clock budget or
-// the iteration cap is spent.  Called by all 32 lanes of one warp (lane 0
+// the iteration cap is spent.  c_best is only ever lowered (a minimum), so a
+// bound offered by another stream while the loop runs is kept.  Called by all 32 lanes of one warp (lane 0
 // chases parents, the warp gathers the path rows); returns, on lane 0,
 // whether the run stops.
 // ---------------------------------------------------------------------------
@@ -976,10 +1010,16 @@ __device__ __forceinline__ bool aox_step_warp(const DevProblem &P, Ctl *ctl, con
         const unsigned long long key = ctl->goal_key;
         *s_found = 0;
         *s_len = 0;
-        if (key != kNoKey) {
+        // a bound offered from outside during this iteration (pakr_plan_offer_bound) may already
+        // be below the child's cost: then the child improves nothing and the tree goes on
+        const float cur = *reinterpret_cast<volatile float *>(&ctl->c_best);
+        if (key != kNoKey && __uint_as_float((uint32_t)(key >> 32)) < cur) {
             const float c = __uint_as_float((uint32_t)(key >> 32));
             const int node = (int)(uint32_t)(key & 0xFFFFFFFFull);
-            ctl->c_best = c;
+            // costs are non-negative, so their bit patterns order like the values: the minimum
+            // keeps an offer that lands in between
+            atomicMin(reinterpret_cast<int *>(&ctl->c_best), __float_as_int(c));
+            ctl->sol_best = c;
             const int ns = ctl->n_solutions;
             if (ns < B.hist_cap) {
                 B.hist_t[ns] = now - ctl->t0_ns;
@@ -1086,6 +1126,7 @@ __device__ __forceinline__ bool aox_init_one(const DevProblem &P, Ctl *ctl, cons
     ctl->iteration = 0u;
     ctl->seed = seed;
     ctl->c_best = c_best_init;
+    ctl->sol_best = __int_as_float(0x7f800000);
     ctl->iterations_done = 0;
     ctl->n_solutions = 0;
     ctl->n_restarts = 0;

@@ -128,7 +128,8 @@ struct Ctl {
     unsigned tc_flag;        // a tree node lies outside the box bound of the tensor-core filter
     float x_goal[kMaxD];
     // AO-x plan state
-    float c_best;
+    float c_best;            // the AO-x bound: own solutions and bounds offered from outside (a minimum)
+    float sol_best;          // cost of this run's own best solution (+inf if none)
     int plan_stop;
     long long iterations_done;
     unsigned long long t0_ns;
@@ -208,6 +209,8 @@ cudaError_t launch_plan_step(const DevProblem &P, Ctl *ctl, const DevTree &T, co
                              const DevPlanBufs &B, cudaGraphConditionalHandle h, cudaStream_t s,
                              const cudaGraphConditionalHandle *inner = nullptr);
 cudaError_t launch_truncate(Ctl *ctl, int count, cudaStream_t s);
+cudaError_t launch_offer_bound(Ctl *ctl, const float *cost, cudaStream_t s);
+cudaError_t preload_offer_bound();
 cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int64_t n, cudaStream_t s);
 
 // Sets the calling thread's pakr_last_error() message (pakr_api.cu).

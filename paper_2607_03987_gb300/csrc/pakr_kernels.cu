@@ -171,6 +171,17 @@ __global__ void k_plan_cont(const Ctl *ctl, cudaGraphConditionalHandle h)
         cudaGraphSetConditional(h, ctl->plan_stop ? 0u : 1u);
 }
 
+// Lowers the AO-x bound to *cost if that is smaller (a finite, non-negative cost; the bit
+// patterns of such floats order like the values).
+__global__ void k_offer_bound(Ctl *ctl, const float *cost)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const float c = *cost;
+        if (c >= 0.f && c < __int_as_float(0x7f800000))
+            atomicMin(reinterpret_cast<int *>(&ctl->c_best), __float_as_int(c));
+    }
+}
+
 __global__ void k_truncate(Ctl *ctl, int count)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0 && count < ctl->count)
@@ -311,6 +322,20 @@ cudaError_t launch_plan_step(const DevProblem &P, Ctl *ctl, const DevTree &T, co
 cudaError_t launch_plan_cont(const Ctl *ctl, cudaGraphConditionalHandle h, cudaStream_t s)
 {
     k_plan_cont<<<1, 32, 0, s>>>(ctl, h);
+    return cudaGetLastError();
+}
+
+// Loads k_offer_bound's GPU code now: a first launch would load it lazily, and loading code can
+// wait for kernels that are running, such as the AO-x graph the offer is meant for.
+cudaError_t preload_offer_bound()
+{
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, k_offer_bound);
+}
+
+cudaError_t launch_offer_bound(Ctl *ctl, const float *cost, cudaStream_t s)
+{
+    k_offer_bound<<<1, 32, 0, s>>>(ctl, cost);
     return cudaGetLastError();
 }
 

@@ -389,11 +389,13 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
         }
         __syncwarp();
     } else if (warp >= kTcReader0) {
+        // the query's coordinates are needed here for the band only, and again by the resolve:
+        // they are recomputed there rather than kept in registers through the tile loop
         float qc2 = 0.f;
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            qv[a] = (qid < K) ? __fsub_rn(__fmul_rn(W.xr[(size_t)a * K + qid], P.sw[a]), P.tc_c[a]) : 0.f;
-            qc2 = __fmaf_rn(qv[a], qv[a], qc2);
+            const float v = (qid < K) ? __fsub_rn(__fmul_rn(W.xr[(size_t)a * K + qid], P.sw[a]), P.tc_c[a]) : 0.f;
+            qc2 = __fmaf_rn(v, v, qc2);
         }
         const float Rq = sqrtf(qc2) * 1.0001f + sqrtf(P.tc_xbox2);
         band = 2.f * tc_bound_coef<D>() * Rq * Rq;
@@ -481,6 +483,9 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
 
     // ---- exact resolve of the candidate groups ----
     if (!flagged && warp >= kTcReader0 && qid < K && (m1 < kTcEligible || s_ovf[qrow])) {
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            qv[a] = __fsub_rn(__fmul_rn(W.xr[(size_t)a * K + qid], P.sw[a]), P.tc_c[a]);
         // against the smallest filter value any chunk has published by now (this chunk's
         // included): groups above it by more than the band cannot hold the nearest node
         const float thrf = (W.nn_amin ? fminf(m1, tc_unord(__ldcg(W.nn_amin + qid))) : m1) + band;

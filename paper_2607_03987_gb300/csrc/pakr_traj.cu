@@ -512,11 +512,7 @@ __global__ void __launch_bounds__(32 * kTrajWarpsPerBlock)
         for (int a = 0; a < PD; ++a)
             xp[a] = x[a];
         rk4_step<DYN>(x, u, P.dt, P);
-        float dd = 0.f;
-#pragma unroll
-        for (int a = 0; a < PD; ++a)
-            dd += (x[a] - xp[a]) * (x[a] - xp[a]);
-        len += sqrtf(dd);
+        len += sqrtf(sq_dist<PD>(x, xp));  // the planner's path-length increment, rounded the same way
         bool inb = true;
 #pragma unroll
         for (int a = 0; a < D; ++a)

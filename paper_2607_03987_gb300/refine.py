@@ -185,3 +185,68 @@ def refined_aox(planner, spec, budget_s, seed=0, refine_iters=15, rounds=(0.3, 0
                 best = dict(x0=best["x0"], controls=out[0].detach().cpu().numpy(), steps=best["steps"])
             history.append((time.perf_counter() - t0, best_cost))
     return best_cost, history, gain, best
+
+
+def refined_aox_concurrent(planner, ref_planner, spec, budget_s, seed=0, refine_iters=15,
+                           rounds=(0.15, 0.35, 0.55, 0.75)):
+    """AO-x with gradient refinement running beside it, within one wall-clock budget.
+
+    The device AO-x loop runs in slices ending at the given fractions of the budget (and the
+    last at the whole budget), each continued from the best cost so far.  While a slice runs on
+    the planner's stream (driven from a host thread; the C call releases the GIL), the best
+    path of the slices before is refined on ref_planner's stream (another planner of the same
+    problem, with its own non-default stream), and a shorter refined path is offered to the
+    running loop as its new bound (pakr_plan_offer_bound), which picks it up at its next
+    iteration.  The refinement therefore takes no time from the search.  planner and ref_planner
+    must use different non-blocking streams.  Returns (best cost, [(elapsed s, cost)], total
+    refinement gain, best path as dict(x0, controls, steps) or None)."""
+    import threading
+    import time
+
+    dev = torch.device(f"cuda:{planner.device}")
+    # device memory for the offered cost is taken, and the fill kernel run once, before any
+    # slice runs: an allocation, or a kernel's first launch (its code is loaded lazily), while the
+    # AO-x graph runs may wait for the graph.  Call this once untimed to warm up the refinement's
+    # own kernels the same way.
+    with torch.cuda.stream(ref_planner.stream):
+        cost_dev = torch.empty(1, dtype=torch.float32, device=dev)
+        cost_dev.fill_(float("inf"))
+    ref_planner.stream.synchronize()
+    t0 = time.perf_counter()
+    history = []
+    best, best_cost, gain = None, float("inf"), 0.0
+    fresh = False
+    fracs = tuple(rounds) + (1.0,)
+    for i, frac in enumerate(fracs):
+        left = frac * budget_s - (time.perf_counter() - t0)
+        if left <= 0:
+            continue
+        out_slice = []
+
+        def run_slice(left=left, i=i, bound=None if best is None else best_cost):
+            out_slice.append(planner.plan(spec["x_init"], spec["x_goal"], budget_s=left, seed=seed + i,
+                                          initial_bound=bound))
+
+        th = threading.Thread(target=run_slice)
+        th.start()
+        if fresh:
+            fresh = False
+            with torch.cuda.stream(ref_planner.stream):
+                ref = refine_path(ref_planner, spec, best, spec["x_goal"], iters=refine_iters)
+                if ref is not None and ref[1] < best_cost:
+                    gain += best_cost - ref[1]
+                    best_cost = ref[1]
+                    best = dict(x0=best["x0"], controls=ref[0].detach().cpu().numpy(), steps=best["steps"])
+                    cost_dev.fill_(best_cost)
+                    planner.offer_bound(cost_dev, ref_planner.stream)
+                    ref_planner.stream.synchronize()
+            history.append((time.perf_counter() - t0, best_cost))
+        th.join()
+        r = out_slice[0]
+        if r["n_solutions"] and float(r["cost"]) < best_cost:
+            best_cost = float(r["cost"])
+            best = dict(x0=r["states"][0].copy(), controls=r["controls"].copy(), steps=r["steps"].copy(),
+                        states=r["states"].copy())
+            fresh = True
+        history.append((time.perf_counter() - t0, best_cost))
+    return best_cost, history, gain, best

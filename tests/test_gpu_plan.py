@@ -135,3 +135,71 @@ def test_quadrotor_table4_shapes(cuda_lib, B, A):
         assert np.allclose(s[0], spec["x_init"])
         assert np.linalg.norm(s[-1][:pd] - spec["x_goal"][:pd]) <= spec["goal_r"] * (1 + 1e-5)
     planner.close()
+
+
+def test_offer_bound_reaches_running_plan(cuda_lib):
+    """A bound offered from another stream and host thread while the device AO-x loop runs is
+    picked up by the loop: a bound just under the straight-line lower bound can be beaten by no
+    path (every node's f = g + h is at least that lower bound), so the loop finds no eligible
+    node from then on and the run ends
+    long before its 5 s budget; the run's own best path keeps its own cost."""
+    import threading
+    import time
+
+    import torch
+
+    spec = W.problem("di3", env_seed=0)
+    s_plan, s_side = torch.cuda.Stream(), torch.cuda.Stream()
+    planner = pakr.Planner(spec, stream=s_plan)
+    planner.plan(spec["x_init"], spec["x_goal"], budget_s=0.05, seed=1)  # builds the graph
+    pd = spec["pdim"]
+    lb = float(np.linalg.norm(spec["x_goal"][:pd] - spec["x_init"][:pd]) - spec["goal_r"])
+    offer = float(np.float32(lb * (1 - 1e-4)))  # below every node's f, rounding included
+    res = []
+    # the offered value is on the device before the plan starts: an allocation, or the first
+    # launch of a kernel (its code is loaded lazily), while the plan runs may wait for it
+    with torch.cuda.stream(s_side):
+        cost = torch.full((1,), offer, dtype=torch.float32, device="cuda")
+    s_side.synchronize()
+    th = threading.Thread(target=lambda: res.append(planner.plan(spec["x_init"], spec["x_goal"], budget_s=5.0,
+                                                                 seed=3)))
+    t0 = time.perf_counter()
+    th.start()
+    time.sleep(0.05)
+    planner.offer_bound(cost, s_side)
+    s_side.synchronize()
+    th.join()
+    elapsed = time.perf_counter() - t0
+    r = res[0]
+    planner.close()
+    assert r["t_total_s"] < 1.0 and elapsed < 2.0, (r["t_total_s"], elapsed)
+    assert r["n_solutions"] > 0 and r["cost"] > lb
+    assert np.all(np.diff(r["history_cost"]) < 0)
+    check_path_properties(spec, r)
+
+
+def test_refined_aox_concurrent_paths_valid(cuda_lib):
+    """AO-x with refinement running beside it on a second stream: the returned path passes the
+    FP64 re-check (valid at every substep, in the goal ball) with the returned cost, and the
+    best cost never rises."""
+    import torch
+
+    from paper_2607_03987_gb300 import refine
+    from recheck import replay_path
+
+    spec = W.problem("di3", env_seed=0, n_boxes=150)
+    planner = pakr.Planner(spec, stream=torch.cuda.Stream())
+    ref_planner = pakr.Planner(W.with_sizes(spec, K=1, k=1, cap=16), stream=torch.cuda.Stream())
+    try:
+        for seed in range(3):
+            c, hist, gain, best = refine.refined_aox_concurrent(planner, ref_planner, spec, 0.1, seed=seed)
+            if best is None:
+                continue
+            costs = [h[1] for h in hist]
+            assert all(b <= a for a, b in zip(costs, costs[1:])), hist
+            rp = replay_path(spec, best["x0"], best["controls"], best["steps"])
+            assert rp["replay_valid"] and rp["replay_in_goal"], rp
+            assert abs(rp["replay_length"] - c) <= 1e-4 * max(1.0, c), (rp, c)
+    finally:
+        planner.close()
+        ref_planner.close()
