@@ -137,6 +137,9 @@ NN_DRAM_BYTES_NCU = 68.143e6 + 3.242e6
 NN_DRAM_SOURCE = ("profiles/k_nn_tc_di3_n1M.md, current kernel (split packed layout, group minima from "
                   "tcgen05.ld.red): dram__bytes_read.sum + dram__bytes_write.sum of one launch")
 
+# Bytes of the planner's device control block that pakr_expand and pakr_plan read back.
+CTL_BYTES = 216
+
 # Nominal dense TF32 / BF16 tensor throughput ratio (1.1 / 2.25 PFLOP/s): the TF32 peak is
 # the measured BF16 GEMM rate times this.
 TF32_PER_BF16 = 1.1 / 2.25
@@ -526,11 +529,11 @@ def adjoint_bench(dev, stream, T=1024, N=200, reps=20):
 
 
 def refined_vs_plain(dev, stream, budget_s=0.1, seeds=10, n_boxes=50):
-    """AO-x path cost after the same wall-clock budget: plain pakr_plan vs AO-x with gradient
-    refinement running beside it on a second stream (refine.refined_aox_concurrent: each new
-    best path is refined while the loop goes on, and a shorter refined path is offered to the
-    running loop as its bound).  The paths of both are kept for the oracle's re-check in the CPU
-    leg."""
+    """AO-x path cost after the same wall-clock budget: plain pakr_plan vs the same AO-x run
+    (same seed, same random numbers) with gradient refinement beside it (refine.refined_aox_live:
+    the run's best path is read while it runs, refined on a second stream, and a shorter refined
+    path is offered to the running loop as its bound).  The paths of both are kept for the
+    oracle's re-check in the CPU leg."""
     import torch
 
     from paper_2607_03987_gb300 import pakr, refine
@@ -540,7 +543,7 @@ def refined_vs_plain(dev, stream, budget_s=0.1, seeds=10, n_boxes=50):
     s_plan, s_side = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     planner = pakr.Planner(spec, device=dev, stream=s_plan)
     ref_planner = pakr.Planner(W.with_sizes(spec, K=1, k=1, cap=16), device=dev, stream=s_side)
-    refine.refined_aox_concurrent(planner, ref_planner, spec, 0.05, seed=999)  # warm-up (graphs, torch kernels)
+    refine.refined_aox_live(planner, ref_planner, spec, 0.05, seed=999)  # warm-up (graphs, torch kernels)
     plain, refined, gains, t_plain, t_ref = [], [], [], [], []
     pending = {"spec": spec, "plain": [], "refined": []}
     for sd in range(seeds):
@@ -551,7 +554,7 @@ def refined_vs_plain(dev, stream, budget_s=0.1, seeds=10, n_boxes=50):
         if r["n_solutions"]:
             pending["plain"].append((r["states"][0], r["controls"], r["steps"], float(r["cost"])))
         t0 = time.perf_counter()
-        c, hist, gain, best = refine.refined_aox_concurrent(planner, ref_planner, spec, budget_s, seed=sd)
+        c, gain, best = refine.refined_aox_live(planner, ref_planner, spec, budget_s, seed=sd)
         t_ref.append(time.perf_counter() - t0)
         refined.append(c)
         gains.append(gain)
@@ -593,7 +596,7 @@ def planning_metrics(dev, stream, name, ttfs_trials, aox_trials, rank=0, aox_bud
             ttfs_host.append(th * 1e3)
             iters.append(r["iterations_first_solution"])
             ne = r["n_edges"]
-            d2h.append(200 + 20 + (ne + 1) * spec["d"] * 4 + ne * (spec["m"] * 4 + 4))
+            d2h.append(CTL_BYTES + 20 + (ne + 1) * spec["d"] * 4 + ne * (spec["m"] * 4 + 4))
     grid_ms = [1, 2, 5, 10, 20, 50, 100]
     costs, n_sol, curves = [], [], []
     for sd in range(aox_trials):
@@ -858,10 +861,10 @@ def main():
                        "parallelism": f"replicas x{ws}"},
             "nodes_appended_per_step": float(np.mean(appended)) if appended else None,
             "roofline": roofline,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12, "d2h_bytes_per_step": 200,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12, "d2h_bytes_per_step": CTL_BYTES,
                     "how": "pakr_expand through the C ABI on host arguments, host wall clock per step: the cost "
                            "bound (4 B) and seed (8 B) go to the device as the expansion graph's kernel "
-                           "parameters, the 200-byte control block comes back to the host to fill the caller's "
+                           "parameters, the 216-byte control block comes back to the host to fill the caller's "
                            "pakr_expand_info, the stream is synchronised; the tree stays resident"},
             "gpu_launches": launches,
             "clocks": clk,
@@ -881,7 +884,7 @@ def main():
                                 "clock through pakr_plan, di3)",
                                 "h2d_bytes_per_step": 160, "d2h_bytes_per_step": e2p["d2h_bytes_mean"],
                                 "how": "pakr_plan with host x_init / x_goal (160-byte parameter block copied to the "
-                                       "device), the path, its history and the 200-byte control block copied back"}
+                                       "device), the path, its history and the control block copied back"}
     if rank == 0:
         if not args.no_sweep:
             line["by_tree_size"] = tree_size_sweep(dev, stream)

@@ -261,8 +261,8 @@ pakr_status pakr_plan_bounded(pakr_planner *planner, const float *x_init, const 
  * kernel on cuda_stream (NULL = default stream), which should be another
  * stream than the planner's, so that it runs while the plan's graph runs; the
  * loop picks the bound up at its next iteration, and nodes and children that
- * can no longer beat it are pruned from then on.  This is the one call that
- * may be made from another host thread while pakr_plan runs on this planner.
+ * can no longer beat it are pruned from then on.  It may be made from another
+ * host thread while pakr_plan runs on this planner.
  * The kernel's GPU code is loaded at pakr_create, so the call loads nothing
  * (a first, lazy load could wait for the running plan); the caller should
  * likewise allocate cost_dev, and launch once any kernel of its own that
@@ -270,8 +270,28 @@ pakr_status pakr_plan_bounded(pakr_planner *planner, const float *x_init, const 
  * overwritten by its start (pass such a bound as initial_bound instead); one that lands
  * after the plan ended is kept until the next plan starts.  A non-finite or
  * negative cost is ignored.  pakr_path.cost stays the cost of the run's own
- * best path.  PAKR_ERR_INVALID_ARG for NULL arguments. */
+ * best path.  PAKR_ERR_INVALID_ARG for NULL arguments.  Besides
+ * pakr_plan_snapshot, this is the one call that may be made while the plan
+ * runs. */
 pakr_status pakr_plan_offer_bound(pakr_planner *planner, const float *cost_dev, void *cuda_stream);
+
+/* Copy the current best path of a pakr_plan / pakr_plan_bounded run on this
+ * planner, which may still be running, into caller device buffers: states
+ * ((n_edges + 1) x d), controls (n_edges x m), steps (n_edges), capacities
+ * for max_edges edges, and info (4 int32): info[0] = 1 if the copy is one
+ * whole path (0 if there is none yet, it has more than max_edges edges, or a
+ * newer path replaced it while it was copied: the AO-x step marks the path's
+ * rows as being written with a sequence number), info[1] = n_edges,
+ * info[2] = the sequence number (it grows with every new best path of the
+ * run), info[3] = the path's cost as float bits.  For refining AO-x solutions
+ * beside the running loop (the paper has no counterpart).  Only enqueues one
+ * small kernel on cuda_stream (another stream than the planner's, so that it
+ * runs while the plan does); like pakr_plan_offer_bound it may be called from
+ * another host thread while the plan runs, its code is loaded at pakr_create,
+ * and the caller's buffers should exist before the plan starts.
+ * PAKR_ERR_INVALID_ARG for NULL buffers or max_edges < 1. */
+pakr_status pakr_plan_snapshot(pakr_planner *planner, float *states_dev, float *controls_dev, int32_t *steps_dev,
+                               int32_t max_edges, int32_t *info_dev, void *cuda_stream);
 
 /* Current node count of the tree (and the expansion counter, if iteration is
  * not NULL).  Synchronises the stream; reads two words, not the tree.

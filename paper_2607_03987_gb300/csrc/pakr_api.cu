@@ -901,6 +901,8 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
         P.grid_items = (const unsigned short *)(b + L.grid_items);
     }
     e = preload_offer_bound();
+    if (e == cudaSuccess)
+        e = preload_plan_snapshot();
     if (e != cudaSuccess)
         return cleanup(fail(PAKR_ERR_CUDA, "loading the bound-offer kernel failed: %s", cudaGetErrorString(e)));
     e = cudaMemset(p->ctl, 0, sizeof(Ctl));
@@ -1168,6 +1170,17 @@ pakr_status pakr_plan_offer_bound(pakr_planner *p, const float *cost_dev, void *
         return fail(PAKR_ERR_INVALID_ARG, "NULL argument");
     DeviceGuard guard(p->device);
     CUDA_TRY(launch_offer_bound(p->ctl, cost_dev, (cudaStream_t)cuda_stream));
+    return PAKR_OK;
+}
+
+pakr_status pakr_plan_snapshot(pakr_planner *p, float *states_dev, float *controls_dev, int32_t *steps_dev,
+                               int32_t max_edges, int32_t *info_dev, void *cuda_stream)
+{
+    if (!p || !states_dev || !controls_dev || !steps_dev || !info_dev || max_edges < 1)
+        return fail(PAKR_ERR_INVALID_ARG, "NULL buffer or max_edges < 1");
+    DeviceGuard guard(p->device);
+    CUDA_TRY(launch_plan_snapshot(p->ctl, p->B, p->di.d, p->di.m, states_dev, controls_dev, steps_dev,
+                                  std::min(max_edges, p->path_cap), info_dev, (cudaStream_t)cuda_stream));
     return PAKR_OK;
 }
 

@@ -1016,6 +1016,11 @@ __device__ __forceinline__ bool aox_step_warp(const DevProblem &P, Ctl *ctl, con
         if (key != kNoKey && __uint_as_float((uint32_t)(key >> 32)) < cur) {
             const float c = __uint_as_float((uint32_t)(key >> 32));
             const int node = (int)(uint32_t)(key & 0xFFFFFFFFull);
+            // a new best path and its cost are being written: the sequence turns odd
+            // (pakr_plan_snapshot discards what it copies meanwhile) and even again once the
+            // rows are out
+            ctl->path_seq = ctl->path_seq + 1u;
+            __threadfence();
             // costs are non-negative, so their bit patterns order like the values: the minimum
             // keeps an offer that lands in between
             atomicMin(reinterpret_cast<int *>(&ctl->c_best), __float_as_int(c));
@@ -1064,12 +1069,15 @@ __device__ __forceinline__ bool aox_step_warp(const DevProblem &P, Ctl *ctl, con
             B.path_u[(size_t)t * M + a] = T.U[(size_t)a * P.cap + v];
         B.path_steps[t] = T.steps[v];
     }
+    __threadfence();
     __syncwarp();
     bool stop = false;
     if (lane == 0) {
         const unsigned long long now = globaltimer_ns();
         bool restart = false;
         const bool found = *s_found != 0;
+        if (found)
+            ctl->path_seq = ctl->path_seq + 1u;
         if (found) {
             restart = true;
             if (stop_at_first) {
@@ -1131,6 +1139,7 @@ __device__ __forceinline__ bool aox_init_one(const DevProblem &P, Ctl *ctl, cons
     ctl->n_solutions = 0;
     ctl->n_restarts = 0;
     ctl->path_len = 0;
+    ctl->path_seq = 0u;
     ctl->err = 0;
     ctl->t_first_ns = ~0ull;
     ctl->nodes_first = -1;

@@ -19,7 +19,10 @@ enum { COST_PATH_LENGTH = 0, COST_DURATION = 1 };
 enum { H_POSITION = 0, H_FULLSTATE = 1 };
 enum { MODE_EXPAND = 0, MODE_PLAN = 1 };
 enum { ERR_PATH_CYCLE = 1, ERR_BAD_PARENT = 2, ERR_TC_TIMEOUT = 4 };
-constexpr int kTcCtasPerSm = 2;  // resident tensor-core nearest-neighbour CTAs per SM
+#ifndef PAKR_TC_ONE_CTA
+#define PAKR_TC_ONE_CTA 0
+#endif
+constexpr int kTcCtasPerSm = PAKR_TC_ONE_CTA ? 1 : 2;  // resident tensor-core nearest-neighbour CTAs per SM
 constexpr int kMaxPropLanes = 16;  // lanes per rollout in k_propagate at most
 // Largest tree (and nearest-neighbour node count) the kernels take: their node indices and
 // chunk arithmetic are 32-bit, and rounding a chunk or a tile up past the last node adds at
@@ -140,6 +143,7 @@ struct Ctl {
     int n_solutions;
     int n_restarts;
     int path_len;            // nodes on the best path (edges + 1); negative = required length when too long
+    unsigned path_seq;       // odd while the AO-x step writes a new best path, even otherwise
     int plan_status;         // 0 running/budget, 1 goal at stop_at_first, 3 no eligible, -1 invalid start
 };
 
@@ -211,6 +215,10 @@ cudaError_t launch_plan_step(const DevProblem &P, Ctl *ctl, const DevTree &T, co
 cudaError_t launch_truncate(Ctl *ctl, int count, cudaStream_t s);
 cudaError_t launch_offer_bound(Ctl *ctl, const float *cost, cudaStream_t s);
 cudaError_t preload_offer_bound();
+// Copy of the best path of a running plan (pakr_plan_snapshot; pakr_kernels.cu).
+cudaError_t launch_plan_snapshot(const Ctl *ctl, const DevPlanBufs &B, int d, int m, float *states,
+                                 float *controls, int *steps, int max_edges, int *info, cudaStream_t s);
+cudaError_t preload_plan_snapshot();
 cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, int64_t n, cudaStream_t s);
 
 // Sets the calling thread's pakr_last_error() message (pakr_api.cu).

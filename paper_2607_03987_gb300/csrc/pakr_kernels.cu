@@ -182,6 +182,61 @@ __global__ void k_offer_bound(Ctl *ctl, const float *cost)
     }
 }
 
+// One warp copies the best path of a plan that may be running on another stream, under the
+// path sequence: info = (1 if the copy is whole, edges, sequence, cost bits); a copy that a new
+// path overwrote meanwhile, or an empty or oversized path, gives info[0] = 0.
+__global__ void k_plan_snapshot(const Ctl *ctl, DevPlanBufs B, int d, int m, float *states, float *controls,
+                                int *steps, int max_edges, int *info)
+{
+    const int lane = threadIdx.x;
+    __shared__ unsigned s_seq;
+    __shared__ int s_len;
+    __shared__ float s_cost;
+    if (lane == 0) {
+        s_seq = __ldcg(&ctl->path_seq);
+        __threadfence();
+        s_len = __ldcg(&ctl->path_len);
+        s_cost = __ldcg(&ctl->sol_best);
+    }
+    __syncwarp();
+    const unsigned seq = s_seq;
+    const int len = s_len;
+    const bool ok = !(seq & 1u) && len > 0 && len - 1 <= max_edges;
+    if (ok) {
+        for (int t = lane; t < len; t += 32) {
+            for (int a = 0; a < d; ++a)
+                states[(size_t)t * d + a] = __ldcg(B.path_x + (size_t)t * d + a);
+            if (t > 0) {
+                for (int a = 0; a < m; ++a)
+                    controls[(size_t)(t - 1) * m + a] = __ldcg(B.path_u + (size_t)t * m + a);
+                steps[t - 1] = __ldcg(B.path_steps + t);
+            }
+        }
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) {
+        const unsigned seq2 = __ldcg(&ctl->path_seq);
+        info[0] = (ok && seq2 == seq) ? 1 : 0;
+        info[1] = len - 1;
+        info[2] = (int)seq;
+        info[3] = __float_as_int(s_cost);
+    }
+}
+
+cudaError_t launch_plan_snapshot(const Ctl *ctl, const DevPlanBufs &B, int d, int m, float *states,
+                                 float *controls, int *steps, int max_edges, int *info, cudaStream_t s)
+{
+    k_plan_snapshot<<<1, 32, 0, s>>>(ctl, B, d, m, states, controls, steps, max_edges, info);
+    return cudaGetLastError();
+}
+
+cudaError_t preload_plan_snapshot()
+{
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, k_plan_snapshot);
+}
+
 __global__ void k_truncate(Ctl *ctl, int count)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0 && count < ctl->count)

@@ -196,8 +196,8 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
 constexpr int kTcM = 128;        // queries per CTA (MMA M)
 constexpr int kTcN = 256;        // nodes per tile of the packed operand copy
 constexpr int kTcBN = 128;       // nodes per pipeline stage and MMA (N): half a packed tile
-constexpr int kTcAcc = 2;        // accumulators of kTcBN columns per CTA
-constexpr int kTcCols = kTcAcc * kTcBN;  // TMEM columns per CTA: two CTAs share an SM's 512
+constexpr int kTcAcc = 4 / kTcCtasPerSm;  // accumulators of kTcBN columns per CTA: an SM's 512 columns
+constexpr int kTcCols = kTcAcc * kTcBN;  // TMEM columns per CTA
 constexpr int kTcG = 16;         // nodes per filter group
 constexpr int kTcRing = 8;       // candidate groups remembered per (query, reader)
 constexpr float kTcSentinel = 1.2676506e30f;  // 2^100: |x - c|^2 of ineligible and padding nodes

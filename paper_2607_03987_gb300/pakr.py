@@ -109,7 +109,7 @@ class BatchResult(C.Structure):
 
 EXPORTED = [
     "pakr_workspace_size", "pakr_create", "pakr_destroy", "pakr_last_error", "pakr_tree_reset",
-    "pakr_expand", "pakr_plan", "pakr_plan_bounded", "pakr_plan_offer_bound", "pakr_tree_export", "pakr_tree_size", "pakr_tree_import", "pakr_tree_truncate", "pakr_debug_last_expand",
+    "pakr_expand", "pakr_plan", "pakr_plan_bounded", "pakr_plan_offer_bound", "pakr_plan_snapshot", "pakr_tree_export", "pakr_tree_size", "pakr_tree_import", "pakr_tree_truncate", "pakr_debug_last_expand",
     "pakr_set_profiling", "pakr_kernel_times", "pakr_philox4x32_10", "pakr_nearest_static", "pakr_version",
     "pakr_batch_create", "pakr_batch_destroy", "pakr_batch_plan", "pakr_batch_path", "pakr_batch_autotune",
     "pakr_batch_set_tuning", "pakr_traj_cost", "pakr_traj_grad", "pakr_traj_checkpoint_floats", "pakr_traj_check",
@@ -143,6 +143,8 @@ def lib():
     L.pakr_plan_bounded.argtypes = [C.c_void_p, _PF, _PF, C.c_double, C.c_int64, C.c_uint64, C.c_uint32, C.c_float,
                                     C.POINTER(Path)]
     L.pakr_plan_offer_bound.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    L.pakr_plan_snapshot.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                     C.c_void_p]
     L.pakr_tree_export.argtypes = [C.c_void_p, C.POINTER(TreeHost)]
     L.pakr_tree_import.argtypes = [C.c_void_p, C.POINTER(TreeHost), _PF]
     L.pakr_tree_truncate.argtypes = [C.c_void_p, C.c_int64]
@@ -337,6 +339,15 @@ class Planner:
         float32 device tensor, enqueued on another torch stream (pakr_plan_offer_bound)."""
         return _check(lib().pakr_plan_offer_bound(self.h, C.c_void_p(cost.data_ptr()),
                                                   C.c_void_p(stream.cuda_stream)), "pakr_plan_offer_bound")
+
+    def plan_snapshot(self, states, controls, steps, info, stream):
+        """Copy the best path of a plan running on this planner into device tensors (states
+        [(E+1) x d], controls [E x m], steps [E] int32, info [4] int32), enqueued on another
+        torch stream (pakr_plan_snapshot)."""
+        max_edges = int(steps.numel())
+        return _check(lib().pakr_plan_snapshot(self.h, C.c_void_p(states.data_ptr()), C.c_void_p(controls.data_ptr()),
+                                               C.c_void_p(steps.data_ptr()), max_edges, C.c_void_p(info.data_ptr()),
+                                               C.c_void_p(stream.cuda_stream)), "pakr_plan_snapshot")
 
     def tree_export(self):
         t = TreeHost()

@@ -11,6 +11,7 @@ the planner's own rules (pakr_traj_check) accept it.
 from __future__ import annotations
 
 import ctypes as C
+import time
 
 import numpy as np
 import torch
@@ -104,7 +105,8 @@ def refine_path(planner, spec, path, x_goal, iters=15, candidates=16, step=0.5, 
     controls, tries `candidates` step sizes step * 2^-i along the normalised
     descent direction at once (clamped to the control box) and keeps the
     shortest candidate that the planner's rules accept (valid after every
-    substep, ending in the goal ball) if it is shorter than the current path.
+    substep, ending in the goal ball, here by a relative margin of 1e-4 inside it)
+    if it is shorter than the current path.
     Everything stays on the device; the host reads the result once.  Returns
     (controls, length), or None if no candidate improved the path."""
     dev = torch.device(f"cuda:{planner.device}")
@@ -127,8 +129,17 @@ def refine_path(planner, spec, path, x_goal, iters=15, candidates=16, step=0.5, 
     def per_step(uu):
         return torch.repeat_interleave(uu, reps, dim=-2)
 
-    valid, in_goal, length, _ = traj_check(planner, per_step(u)[None], x0, x_goal)
-    cur = torch.where((valid[0] == 1) & (in_goal[0] == 1), length[0], inf)
+    # a shortened path tends to end on the goal sphere itself; it is accepted only with its end
+    # inside the ball by a relative margin, so that replaying it in another precision stays in
+    pd = spec["pdim"]
+    g_pos = torch.tensor(np.asarray(x_goal, np.float32)[:pd], device=dev)
+    r_in = float(spec["goal_r"]) * (1.0 - 1e-4)
+
+    def inside(xf):
+        return torch.linalg.norm(xf[..., :pd] - g_pos, dim=-1) <= r_in
+
+    valid, in_goal, length, xf0 = traj_check(planner, per_step(u)[None], x0, x_goal)
+    cur = torch.where((valid[0] == 1) & (in_goal[0] == 1) & inside(xf0[0]), length[0], inf)
     start = cur.clone()
     for _ in range(iters):
         uu = u.clone().requires_grad_(True)
@@ -136,8 +147,8 @@ def refine_path(planner, spec, path, x_goal, iters=15, candidates=16, step=0.5, 
         g = uu.grad
         d = g / (g.norm() + 1e-12)
         cand = torch.max(torch.min(u[None] - alphas[:, None, None] * d[None], hi), lo)
-        v, ig, L, _ = traj_check(planner, per_step(cand), xc, x_goal)
-        L = torch.where((v == 1) & (ig == 1), L, inf)
+        v, ig, L, xf = traj_check(planner, per_step(cand), xc, x_goal)
+        L = torch.where((v == 1) & (ig == 1) & inside(xf), L, inf)
         i = torch.argmin(L)
         better = L[i] < cur
         u = torch.where(better, cand[i], u)
@@ -250,3 +261,73 @@ def refined_aox_concurrent(planner, ref_planner, spec, budget_s, seed=0, refine_
             fresh = True
         history.append((time.perf_counter() - t0, best_cost))
     return best_cost, history, gain, best
+
+
+def refined_aox_live(planner, ref_planner, spec, budget_s, seed=0, refine_iters=15, max_edges=1024,
+                     poll_s=0.0005):
+    """One AO-x run with refinement beside it for its whole budget.
+
+    The device AO-x loop runs once, as pakr_plan with this seed would (the same graph, the same
+    random numbers), on the planner's stream, driven from a host thread.  Meanwhile this thread
+    polls the run's best path (pakr_plan_snapshot, on ref_planner's stream); each new one is
+    refined on ref_planner (another planner of the same problem with its own non-default
+    stream) if the last refinement's duration still fits in the budget, and a refined path
+    shorter than everything so far is offered to the running loop as its bound
+    (pakr_plan_offer_bound).  Until the first offer lands the loop does exactly what
+    plain AO-x does; after it, it prunes against the tighter bound.  Returns (best cost,
+    total refinement gain, best path as dict(x0, controls, steps) or None)."""
+    import threading
+
+    d, m = spec["d"], spec["m"]
+    side = ref_planner.stream
+    # every buffer, and every kernel this thread launches, exists or has run once before the
+    # plan starts: an allocation, or a kernel's first (lazy) load, while the plan runs may wait
+    # for it
+    with torch.cuda.stream(side):
+        dev = torch.device(f"cuda:{planner.device}")
+        st = torch.zeros((max_edges + 1, d), dtype=torch.float32, device=dev)
+        ct = torch.zeros((max_edges, m), dtype=torch.float32, device=dev)
+        sp = torch.zeros(max_edges, dtype=torch.int32, device=dev)
+        info = torch.zeros(4, dtype=torch.int32, device=dev)
+        cost_dev = torch.full((1,), float("inf"), dtype=torch.float32, device=dev)
+        planner.plan_snapshot(st, ct, sp, info, side)
+        info.cpu()
+    side.synchronize()
+    res = []
+    th = threading.Thread(target=lambda: res.append(planner.plan(spec["x_init"], spec["x_goal"], budget_s=budget_s,
+                                                                 seed=seed)))
+    t0 = time.perf_counter()
+    th.start()
+    seen, best_ref, best_path, gain = 0, float("inf"), None, 0.0
+    t_refine = 0.0  # duration of the last refinement: one is started only if that much time is left
+    while th.is_alive():
+        with torch.cuda.stream(side):
+            planner.plan_snapshot(st, ct, sp, info, side)
+            inf_h = info.cpu().numpy()
+        if inf_h[0] == 1 and int(inf_h[2]) > seen and time.perf_counter() - t0 + t_refine < budget_s:
+            t_start = time.perf_counter()
+            seen = int(inf_h[2])
+            ne = int(inf_h[1])
+            c = float(np.array([inf_h[3]], dtype=np.int32).view(np.float32)[0])
+            with torch.cuda.stream(side):
+                path = dict(x0=st[0].cpu().numpy(), controls=ct[:ne].cpu().numpy(), steps=sp[:ne].cpu().numpy())
+                ref = refine_path(ref_planner, spec, path, spec["x_goal"], iters=refine_iters)
+                base = min(c, best_ref)
+                if ref is not None and ref[1] < base:
+                    gain += base - ref[1]
+                    best_ref = ref[1]
+                    best_path = dict(x0=path["x0"], controls=ref[0].detach().cpu().numpy(), steps=path["steps"])
+                    cost_dev.fill_(best_ref)
+                    planner.offer_bound(cost_dev, side)
+            side.synchronize()
+            t_refine = time.perf_counter() - t_start
+        else:
+            time.sleep(poll_s)
+    th.join()
+    r = res[0]
+    own = float(r["cost"]) if r["n_solutions"] else float("inf")
+    if best_ref < own:
+        return best_ref, gain, best_path
+    if r["n_solutions"]:
+        return own, gain, dict(x0=r["states"][0].copy(), controls=r["controls"].copy(), steps=r["steps"].copy())
+    return own, gain, None

@@ -203,3 +203,57 @@ def test_refined_aox_concurrent_paths_valid(cuda_lib):
     finally:
         planner.close()
         ref_planner.close()
+
+
+def test_plan_snapshot_copies_best_path(cuda_lib):
+    """pakr_plan_snapshot on another stream returns the plan's best path: after a plan, the
+    copy is whole and equals the path and cost pakr_plan returned."""
+    import torch
+
+    spec = W.problem("di3", env_seed=0)
+    s_plan, s_side = torch.cuda.Stream(), torch.cuda.Stream()
+    planner = pakr.Planner(spec, stream=s_plan)
+    try:
+        r = planner.plan(spec["x_init"], spec["x_goal"], budget_s=0.03, seed=5)
+        assert r["n_solutions"] > 0
+        E = 512
+        with torch.cuda.stream(s_side):
+            st = torch.zeros((E + 1, spec["d"]), dtype=torch.float32, device="cuda")
+            ct = torch.zeros((E, spec["m"]), dtype=torch.float32, device="cuda")
+            sp = torch.zeros(E, dtype=torch.int32, device="cuda")
+            info = torch.zeros(4, dtype=torch.int32, device="cuda")
+            planner.plan_snapshot(st, ct, sp, info, s_side)
+            inf_h = info.cpu().numpy()
+            ne = int(inf_h[1])
+            assert inf_h[0] == 1 and ne == r["n_edges"] and inf_h[2] >= 2 and inf_h[2] % 2 == 0
+            assert np.array_equal(st[: ne + 1].cpu().numpy(), r["states"])
+            assert np.array_equal(ct[:ne].cpu().numpy(), r["controls"])
+            assert np.array_equal(sp[:ne].cpu().numpy(), r["steps"])
+            assert np.array([inf_h[3]], np.int32).view(np.float32)[0] == np.float32(r["cost"])
+    finally:
+        planner.close()
+
+
+def test_refined_aox_live_paths_valid(cuda_lib):
+    """AO-x run once, with the refinement polling its best path beside it and offering shorter
+    refined paths: the returned path passes the FP64 re-check with the returned cost."""
+    import torch
+
+    from paper_2607_03987_gb300 import refine
+    from recheck import replay_path
+
+    spec = W.problem("di3", env_seed=0, n_boxes=150)
+    planner = pakr.Planner(spec, stream=torch.cuda.Stream())
+    ref_planner = pakr.Planner(W.with_sizes(spec, K=1, k=1, cap=16), stream=torch.cuda.Stream())
+    try:
+        refine.refined_aox_live(planner, ref_planner, spec, 0.05, seed=99)  # warm-up
+        for seed in range(3):
+            c, gain, best = refine.refined_aox_live(planner, ref_planner, spec, 0.1, seed=seed)
+            if best is None:
+                continue
+            rp = replay_path(spec, best["x0"], best["controls"], best["steps"])
+            assert rp["replay_valid"] and rp["replay_in_goal"], rp
+            assert abs(rp["replay_length"] - c) <= 1e-4 * max(1.0, c), (rp, c)
+    finally:
+        planner.close()
+        ref_planner.close()
