@@ -133,16 +133,16 @@ def measured_peaks():
 # dram__bytes_read.sum + dram__bytes_write.sum of one tensor-core nearest-neighbour launch
 # (k_nn_tc) on the bench workload (n = 1,000,000 nodes, d = 6), from the ncu capture named in
 # NN_DRAM_SOURCE.  None when the kernel has changed since that capture.
-NN_DRAM_BYTES_NCU = 68.143e6 + 3.242e6
-NN_DRAM_SOURCE = ("profiles/k_nn_tc_di3_n1M.md, current kernel (split packed layout, group minima from "
-                  "tcgen05.ld.red): dram__bytes_read.sum + dram__bytes_write.sum of one launch")
+NN_DRAM_BYTES_NCU = 36.886016e6 + 1.28e3
+NN_DRAM_SOURCE = ("profiles/k_nn_tc_di3_n1M.md, current kernel (FP16 operands, 16 stages): "
+                  "dram__bytes_read.sum + dram__bytes_write.sum of one launch")
 
 # Bytes of the planner's device control block that pakr_expand and pakr_plan read back.
 CTL_BYTES = 216
 
-# Nominal dense TF32 / BF16 tensor throughput ratio (1.1 / 2.25 PFLOP/s): the TF32 peak is
-# the measured BF16 GEMM rate times this.
-TF32_PER_BF16 = 1.1 / 2.25
+# Nominal dense FP16 / BF16 tensor throughput ratio (both 2.25 PFLOP/s): the FP16 peak is the
+# measured BF16 GEMM rate.
+FP16_PER_BF16 = 1.0
 
 
 def nn_flops_per_launch(K, n, d):
@@ -153,25 +153,26 @@ def nn_flops_per_launch(K, n, d):
 
 def nn_tc_filter_flops_per_launch(K, n, d, kt):
     """Tensor-core work of the filter as the kernel forms it: per (query, node) pair kt
-    TF32 multiply-adds (the hi/lo partial products and the two |x|^2 columns)."""
+    FP16 multiply-adds (the hi/lo partial products and the two |x|^2 columns)."""
     return 2.0 * K * n * kt
 
 
 def nn_tc_mma_flops_per_launch(K, n, d, kt, mma_steps):
     """Tensor-core work as issued: queries padded to 128-row blocks, nodes to 256-node
-    tiles, mma_steps MMAs of K = 8 per 128 x 128 block."""
-    return 2.0 * (-(-K // 128) * 128) * (-(-n // 256) * 256) * 8 * mma_steps
+    tiles, mma_steps MMAs of K = 16 per 128 x 128 block."""
+    return 2.0 * (-(-K // 128) * 128) * (-(-n // 256) * 256) * 16 * mma_steps
 
 
 def tc_shape(d):
-    """(columns of the packed node row, MMA k-steps per 128-node stage) of k_nn_tc: the split
-    layout (x_hi, x_lo, |x|^2 hi, lo) with a second query operand against the x_hi columns where
-    it stores fewer columns without more MMAs (d = 3, 5, 6), else (x_hi, x_lo, x_hi, |x|^2)."""
-    joint = ((3 * d + 2) + 7) // 8 * 8
-    split = ((2 * d + 2) + 7) // 8 * 8
-    if split < joint and split // 8 + (d + 7) // 8 <= joint // 8:
-        return split, split // 8 + (d + 7) // 8
-    return joint, joint // 8
+    """(columns of the packed node row, MMA k-steps per 128-node stage) of k_nn_tc: FP16
+    operands, K = 16 per MMA; the split layout (x_hi, x_lo, |x|^2 hi, lo) with a second query
+    operand against the x_hi columns where it stores fewer columns without more MMAs
+    (d = 5, 6, 12), else (x_hi, x_lo, x_hi, |x|^2 hi, lo) (d = 3, 4)."""
+    r16 = lambda c: (c + 15) // 16 * 16
+    joint, split, ka2 = r16(3 * d + 2), r16(2 * d + 2), r16(d)
+    if split < joint and split // 16 + ka2 // 16 <= joint // 16:
+        return split, split // 16 + ka2 // 16
+    return joint, joint // 16
 
 
 def nn_uses_tensor_cores(spec, n):
@@ -814,14 +815,14 @@ def main():
     nn_ms = kernel_ms["k_nn_tc" if tc else "k_nn"]
     method_tflops = nn_flops_per_launch(K, N_PREFILL, d) / (nn_ms * 1e-3) / 1e12
     if tc:
-        tf32_peak = float(peaks["bf16_tflops"]) * TF32_PER_BF16
+        fp16_peak = float(peaks["bf16_tflops"]) * FP16_PER_BF16
         kt_cols, mma_steps = tc_shape(d)
-        roofline = {"bound": "tensor", "achieved": method_tflops, "peak": tf32_peak, "unit": "TFLOP/s",
-                    "frac": method_tflops / tf32_peak, "traffic": NN_DRAM_BYTES_NCU, "kernel": "k_nn_tc",
+        roofline = {"bound": "tensor", "achieved": method_tflops, "peak": fp16_peak, "unit": "TFLOP/s",
+                    "frac": method_tflops / fp16_peak, "traffic": NN_DRAM_BYTES_NCU, "kernel": "k_nn_tc",
                     "work": "3 K n d (a subtract, a multiply and an add per coordinate of every query-node pair), "
                             "the method's own count",
-                    "peak_source": f"TF32 dense = {peak_src} BF16 GEMM {float(peaks['bf16_tflops']):.0f} TFLOP/s "
-                                   f"x nominal TF32/BF16 ratio 1.1/2.25 (of {peak_src})",
+                    "peak_source": f"FP16 dense = {peak_src} BF16 GEMM {float(peaks['bf16_tflops']):.0f} TFLOP/s "
+                                   f"x nominal FP16/BF16 ratio 1 (of {peak_src}; the MMAs are kind::f16)",
                     "traffic_unit": "DRAM bytes read + written per k_nn_tc launch",
                     "traffic_source": NN_DRAM_SOURCE,
                     "filter_tflops_as_formed": nn_tc_filter_flops_per_launch(K, N_PREFILL, d, kt_cols)

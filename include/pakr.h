@@ -85,8 +85,8 @@ typedef enum pakr_heuristic {
 /* Per-rollout outcome of the last expansion (pakr_debug_last_expand). */
 /* Nearest-neighbour kernel choice.  Both give the same result (the exact FP32
  * argmin, lowest index on a tie).  The tensor-core kernel needs a packed
- * operand copy of the tree: 4 * (2d + 2 rounded up to 8) bytes per node for
- * d = 3, 5, 6, and 4 * (3d + 2 rounded up to 8) for d = 4 and 12. */
+ * FP16 operand copy of the tree: 2 * (2d + 2 rounded up to 16) bytes per node for
+ * d = 5, 6 and 12, and 2 * (3d + 2 rounded up to 16) for d = 3 and 4. */
 typedef enum pakr_nn_mode {
     PAKR_NN_AUTO = 0,           /* tensor cores for trees of >= 28672 nodes when n_parents >= 256, FP32 otherwise */
     PAKR_NN_FP32 = 1,           /* FP32 kernel only; no packed copy is kept */

@@ -853,6 +853,7 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
             }
         }
         P.tc_xbox2 = (float)(r2 * 1.0001 + 1e-30);
+        P.tc_s = tc_scale(P.tc_xbox2);
         P.tc_min_n = p->T.XT ? tc_min_nodes(desc) : 0x7FFFFFFF;
         if (p->T.XT) {
             e = tc_configure(P);
@@ -906,6 +907,12 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
     if (e != cudaSuccess)
         return cleanup(fail(PAKR_ERR_CUDA, "loading the bound-offer kernel failed: %s", cudaGetErrorString(e)));
     e = cudaMemset(p->ctl, 0, sizeof(Ctl));
+    // The tensor-core filter stages whole 128-node halves of the packed copy: rows past the
+    // tree are masked by their norm column, but their coordinate columns still enter the
+    // products, so they must hold finite values (zeros here, or rows of earlier nodes after a
+    // truncation), never a stale bit pattern that reads as an infinity.
+    if (e == cudaSuccess && p->T.XT)
+        e = cudaMemset(p->T.XT, 0, L.xr - L.XT);
     if (e != cudaSuccess)
         return cleanup(fail(PAKR_ERR_CUDA, "cudaMemset failed: %s", cudaGetErrorString(e)));
 

@@ -48,6 +48,7 @@ struct DevProblem {
     // smallest tree size that takes the tensor-core kernel (INT_MAX: never)
     float tc_c[kMaxD];
     float tc_xbox2;
+    float tc_s = 1.f;     // power of two the FP16 filter scales centred coordinates by (box radius to [2^7, 2^8))
     int tc_min_n = 0x7FFFFFFF;
     // obstacle grid over the position box (grid_g = 0: none, every obstacle is tested): cell
     // index per position axis a is obstacle_cell(p_a, grid_lo[a], grid_inv[a], grid_g), cells
@@ -196,7 +197,8 @@ cudaError_t launch_nn_fp32(const DevProblem &P, const Ctl *ctl, const DevTree &T
 cudaError_t launch_nn_tc(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
                          cudaStream_t s);
 cudaError_t launch_tc_pack(const DevProblem &P, Ctl *ctl, const DevTree &T, int count, cudaStream_t s);
-int tc_operand_floats(int d);  // floats per packed node row (2d + 2 or 3d + 2 rounded up to 8, pakr_tc.cuh)
+int tc_operand_floats(int d);  // 4-byte words per packed node row (pakr_tc.cuh: TcShape<D>::KT operand elements)
+float tc_scale(float xbox2);   // the FP16 filter's coordinate scale for a box of squared radius xbox2
 cudaError_t tc_configure(const DevProblem &P);
 cudaError_t launch_propagate(const DevProblem &P, Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
                              cudaStream_t s);

@@ -1,4 +1,4 @@
-// k_nn_tc: cost-pruned nearest neighbour on the tensor cores (tcgen05, TF32 hi/lo split).
+// k_nn_tc: cost-pruned nearest neighbour on the tensor cores (tcgen05, FP16 hi/lo split).
 //
 // Same result as k_nn (Algorithm 1 NearestNeighbor over the frozen snapshot,
 // Sec. IV-A, IV-B): for each query the eligible node (f-cost below the bound)
@@ -6,16 +6,17 @@
 //
 // A CTA takes 128 queries (one query block) and a chunk of whole 128-node half tiles of the
 // packed operand copy.  Per half tile the tensor cores compute the filter
-// a = |x - c|^2 - 2 (q - c).(x - c) for all 128 x 128 pairs into TMEM; reader warps take
-// each row's minimum over groups of 16 nodes and remember the groups whose minimum lies
-// within `band` of the row's running minimum (band = 2 * B, B the bound of tc_bound_coef on
-// |a + |q - c|^2 - e|).  After the chunk, every node whose exact distance could be the
-// row's minimum lies in a remembered group (its filter value is at most m1 + band), so
-// recomputing e on those groups gives the exact argmin.  A row whose candidate ring
-// overflowed, or a tree flagged as leaving the box bound, is rescanned exactly by the whole
-// CTA.  Chunk results merge with a 64-bit atomicMin of (distance bits << 32 | index), as in
-// k_nn.  Since a differs from the distance by a per-query constant, the chunks also share a
-// per-query minimum of a (W.nn_amin) and prune their candidates against it.
+// a = |x - c|^2 - 2 (q - c).(x - c) (in coordinates scaled by P.tc_s) for all 128 x 128
+// pairs into TMEM; reader warps take each row's minimum over groups of 16 nodes and remember
+// the groups whose minimum lies within `band` of the row's running minimum (band = 2 * B, B
+// the bound of tc_bound_coef on |a + |q - c|^2 - e|).  After the chunk, every node whose
+// exact distance could be the row's minimum lies in a remembered group (its filter value is
+// at most m1 + band), so recomputing e from the tree's FP32 coordinates on those groups gives
+// the exact argmin.  A row whose candidate ring overflowed or whose query lies outside the
+// filter's range, or a tree flagged as leaving the box bound, is rescanned exactly by the
+// whole CTA.  Chunk results merge with a 64-bit atomicMin of (distance bits << 32 | index),
+// as in k_nn.  Since a differs from the distance by a per-query constant, the chunks also
+// share a per-query minimum of a (W.nn_amin) and prune their candidates against it.
 //
 // Two CTAs share an SM, each with two accumulators of 128 TMEM columns.  Within a CTA the
 // work is one dependency chain (MMA, commit, readers, release, next MMA) whose mbarrier
@@ -25,8 +26,8 @@
 // Roles (TcShape<D>::THREADS: 12 warps per CTA for d <= 8, 8 for larger d):
 //   warp 0 lane 0   bulk-copies packed half tiles (T.XT) and f-costs into a ring of stages;
 //   warp 1 lane 0   waits "stage masked" and the release of the accumulator the tile will use
-//                   (tile t - 2's), then issues KT/8 MMAs (M 128, N 128, K 8);
-//   warps 2-3       mask ineligible rows (|x|^2 columns := 2^100), then signal "stage masked";
+//                   (tile t - 2's), then issues MMAS MMAs (M 128, N 128, K 16);
+//   warps 2-3       mask ineligible rows (|x|^2 hi column := 2^15), then signal "stage masked";
 //   warps 4-        read the accumulators' 16-node group minima with TMEM loads that reduce
 //                   (tcgen05.ld.red min, sm_103a) and keep candidate rings: for d <= 8 two
 //                   warps per TMEM lane quarter, 64 columns each (two reader threads per query
@@ -37,6 +38,8 @@
 // TMEM and leaves, the loader waits (bounded) until every bulk copy it issued has landed and
 // the MMA thread waits (bounded) on a final commit that follows every MMA it issued, so no
 // asynchronous copy or MMA still writes shared memory or TMEM after the CTA is gone.
+#include <cmath>
+
 #include "pakr_device.cuh"
 #include "pakr_tc.cuh"
 
@@ -58,68 +61,33 @@ __device__ __forceinline__ float tc_exact(const DevProblem &P, const DevTree &T,
     return (f < bound) ? acc : __int_as_float(0x7f800000);
 }
 
-// Exact resolve of the 16-node group starting at g0 (a multiple of 16, inside one 256-node
-// tile) from the packed copy: a node's centred coordinate is hi + lo exactly (the copy keeps
-// lo = v - hi untruncated), so this equals tc_exact, and the packed tile was just streamed
-// through L2.  Four nodes at a time, their 16-byte column chunks loaded together.
+// Exact resolve of the 16-node group starting at g0 from the tree's own coordinates (the
+// packed FP16 copy does not hold them exactly): tc_exact per node, four nodes' loads in flight.
 template <int D>
-__device__ __forceinline__ void tc_resolve_group(const DevTree &T, int g0, int end, float bound, const float *qv,
-                                                 float &best, int &bidx)
+__device__ __forceinline__ void tc_resolve_group(const DevProblem &P, const DevTree &T, int g0, int end, float bound,
+                                                 const float *qv, float &best, int &bidx)
 {
-    using S = TcShape<D>;
-    constexpr int NC = (2 * D + 3) / 4;  // 16-byte chunks holding x_hi and x_lo of a row
-    constexpr int RB = 4;                // rows per batch of loads
-    const unsigned char *tile = reinterpret_cast<const unsigned char *>(T.XT) + (size_t)(g0 / kTcN) * S::TILE_BYTES;
-    const int r0 = g0 % kTcN;
-#pragma unroll 1
-    for (int q4 = 0; q4 < kTcG; q4 += 4) {
-        const float4 f4 = *reinterpret_cast<const float4 *>(T.fcost + g0 + q4);
-#pragma unroll
-        for (int g2 = 0; g2 < 4; g2 += RB) {
-            float4 ch[RB][NC];
-#pragma unroll
-            for (int g = 0; g < RB; ++g)
-#pragma unroll
-                for (int c = 0; c < NC; ++c)
-                    ch[g][c] = *reinterpret_cast<const float4 *>(tile + tc_off<D>(r0 + q4 + g2 + g, 4 * c));
-#pragma unroll
-            for (int g = 0; g < RB; ++g) {
-                const float *row = reinterpret_cast<const float *>(ch[g]);
-                float acc = 0.f;
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const float xc = __fadd_rn(row[a], row[D + a]);
-                    const float diff = __fadd_rn(qv[a], -xc);
-                    acc = (a == 0) ? __fmul_rn(diff, diff) : __fmaf_rn(diff, diff, acc);
-                }
-                const int gg = g2 + g;
-                const float f = gg == 0 ? f4.x : gg == 1 ? f4.y : gg == 2 ? f4.z : f4.w;
-                const int j = g0 + q4 + gg;
-                const float ex = (f < bound) ? acc : __int_as_float(0x7f800000);
-                if (j < end && (ex < best || (ex == best && j < bidx))) {
-                    best = ex;
-                    bidx = j;
-                }
-            }
+#pragma unroll 4
+    for (int g = 0; g < kTcG; ++g) {
+        const int j = g0 + g;
+        if (j >= end)
+            break;
+        const float ex = tc_exact<D>(P, T, j, bound, qv);
+        if (ex < best || (ex == best && j < bidx)) {
+            best = ex;
+            bidx = j;
         }
     }
 }
 
-// Bring the packed rows and f-costs of the 16-node group starting at g0 into L2: two 8-row
-// core-matrix groups, each (2d + 3) / 4 16-byte chunks wide (128-byte lines), and one line
-// of f-costs.
+// Bring the coordinates (D arrays, 64 bytes each) and f-costs of the 16-node group starting
+// at g0 into L2.
 template <int D>
-__device__ __forceinline__ void tc_prefetch_group(const DevTree &T, int g0)
+__device__ __forceinline__ void tc_prefetch_group(const DevProblem &P, const DevTree &T, int g0)
 {
-    using S = TcShape<D>;
-    constexpr int NC = (2 * D + 3) / 4;
-    const unsigned char *tile = reinterpret_cast<const unsigned char *>(T.XT) + (size_t)(g0 / kTcN) * S::TILE_BYTES;
-    const int r0 = g0 % kTcN;
 #pragma unroll
-    for (int rg = 0; rg < 2; ++rg)
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(tile + tc_off<D>(r0 + 8 * rg, 4 * c)));
+    for (int a = 0; a < D; ++a)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(T.X + (size_t)a * P.cap + g0));
     asm volatile("prefetch.global.L2 [%0];" ::"l"(T.fcost + g0));
 }
 
@@ -202,8 +170,8 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
     if (tid < kTcM) {
         s_ovf[tid] = 0;
         // query operand: -2 (q - c) split as hi (against x_hi), hi (against x_lo) and lo (against
-        // x_hi), and 1, 1 against |x|^2 hi, lo.  Split layout: (hi, hi, 1, 1) over the node row and
-        // (lo) in the second operand; joint layout: (hi, hi, lo, 1, 1) in one row.
+        // x_hi), and kTcNormA twice against |x|^2 hi, lo.  Split layout: (hi, hi, n, n) over the
+        // node row and (lo) in the second operand; joint layout: (hi, hi, lo, n, n) in one row.
         const int q = qbase + tid;
         float row[KT], row2[S::KA2 > 0 ? S::KA2 : 1];
 #pragma unroll
@@ -212,30 +180,41 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
 #pragma unroll
         for (int k = 0; k < (S::KA2 > 0 ? S::KA2 : 1); ++k)
             row2[k] = 0.f;
-        if (q < K) {
+        // coordinates scaled by P.tc_s; a query farther than 2^9 from the centre in those units
+        // (twice the box radius and more) could leave the range the error bound and the
+        // eligibility threshold assume: its row is rescanned exactly instead
+        float qn = 0.f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const float v = q < K ? (W.xr[(size_t)a * K + q] * P.sw[a] - P.tc_c[a]) * P.tc_s : 0.f;
+            qn = __fmaf_rn(v, v, qn);
+        }
+        if (q < K && !(qn <= kTcQueryMax2)) {
+            s_ovf[tid] = 1;
+        } else if (q < K) {
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                const float v = -2.f * (W.xr[(size_t)a * K + q] * P.sw[a] - P.tc_c[a]);
-                const float hi = tf32_trunc(v);
+                const float v = -2.f * (W.xr[(size_t)a * K + q] * P.sw[a] - P.tc_c[a]) * P.tc_s;
+                float hi, lo;
+                tc_split_val(v, hi, lo);
                 row[a] = hi;
                 row[D + a] = hi;
                 if constexpr (S::SPLIT)
-                    row2[a] = tf32_trunc(v - hi);
+                    row2[a] = lo;
                 else
-                    row[2 * D + a] = tf32_trunc(v - hi);
+                    row[2 * D + a] = lo;
             }
-            row[S::NORM] = 1.f;
-            row[S::NORM + 1] = 1.f;
+            row[S::NORM] = kTcNormA;
+            row[S::NORM + 1] = kTcNormA;
         }
 #pragma unroll
-        for (int c = 0; c < KT / 4; ++c)
-            *reinterpret_cast<float4 *>(sA + tc_off<D>(tid, 4 * c)) =
-                make_float4(row[4 * c], row[4 * c + 1], row[4 * c + 2], row[4 * c + 3]);
+        for (int c = 0; c < KT / kTcCoreK; ++c)
+            *reinterpret_cast<uint4 *>(sA + tc_off<D>(tid, kTcCoreK * c)) = tc_chunk(row + kTcCoreK * c);
         if constexpr (S::SPLIT) {
 #pragma unroll
-            for (int c = 0; c < S::KA2 / 4; ++c)
-                *reinterpret_cast<float4 *>(sA + S::A1_BYTES + tc_off2<D>(tid, 4 * c)) =
-                    make_float4(row2[4 * c], row2[4 * c + 1], row2[4 * c + 2], row2[4 * c + 3]);
+            for (int c = 0; c < S::KA2 / kTcCoreK; ++c)
+                *reinterpret_cast<uint4 *>(sA + S::A1_BYTES + tc_off2<D>(tid, kTcCoreK * c)) =
+                    tc_chunk(row2 + kTcCoreK * c);
         }
         fence_async_smem();
     }
@@ -307,8 +286,8 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
                     const int j = start + t * kTcBN + r;
                     if (!(j < end && sF0[b * kTcBN + r] < bound)) {
                         unsigned char *rowp = sB0 + b * S::STAGE_BYTES;
-                        *reinterpret_cast<float *>(rowp + tc_off<D>(r, S::NORM)) = kTcSentinel;
-                        *reinterpret_cast<float *>(rowp + tc_off<D>(r, S::NORM + 1)) = 0.f;
+                        tc_store_elem(rowp + tc_off<D>(r, S::NORM), kTcSentinel);
+                        tc_store_elem(rowp + tc_off<D>(r, S::NORM + 1), 0.f);
                         wrote = true;
                     }
                 }
@@ -321,7 +300,7 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
         }
     } else if (warp == kTcMmaWarp) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_tf32(kTcM, kTcBN);
+            constexpr uint32_t idesc = idesc_f16(kTcM, kTcBN);
             // descriptors of stage 0 and k-step 0; the start-address field (address / 16, 14 bits)
             // takes the stage and k-step offsets directly (shared addresses stay below 256 KB)
             const uint64_t adesc = smem_desc(smem_u32(sA), S::LBO, S::SBO);
@@ -354,16 +333,16 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
                     }
                     tc_fence_after();
                     const uint32_t dt = tbase + (uint32_t)(ac * kTcBN);
-                    mma_tf32_ss_c<false>(dt, adesc, bd, idesc);
+                    mma_f16_ss_c<false>(dt, adesc, bd, idesc);
 #pragma unroll
-                    for (int s = 1; s < KT / 8; ++s)
-                        mma_tf32_ss_c<true>(dt, adesc + (uint64_t)((2 * S::LBO * s) >> 4),
-                                            bd + (uint64_t)((2 * S::LBO * s) >> 4), idesc);
+                    for (int s = 1; s < KT / kTcKStep; ++s)
+                        mma_f16_ss_c<true>(dt, adesc + (uint64_t)((2 * S::LBO * s) >> 4),
+                                       bd + (uint64_t)((2 * S::LBO * s) >> 4), idesc);
                     // split layout: the lo part of the query against the x_hi columns
 #pragma unroll
-                    for (int s = 0; s < S::KA2 / 8; ++s)
-                        mma_tf32_ss_c<true>(dt, adesc2 + (uint64_t)((2 * S::LBO * s) >> 4),
-                                            bd + (uint64_t)((2 * S::LBO * s) >> 4), idesc);
+                    for (int s = 0; s < S::KA2 / kTcKStep; ++s)
+                        mma_f16_ss_c<true>(dt, adesc2 + (uint64_t)((2 * S::LBO * s) >> 4),
+                                       bd + (uint64_t)((2 * S::LBO * s) >> 4), idesc);
                     mma_commit(free0 + st8);
                     mma_commit(done0 + 8 * ac);
                     st8 += 8;
@@ -397,14 +376,14 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
             const float v = (qid < K) ? __fsub_rn(__fmul_rn(W.xr[(size_t)a * K + qid], P.sw[a]), P.tc_c[a]) : 0.f;
             qc2 = __fmaf_rn(v, v, qc2);
         }
-        const float Rq = sqrtf(qc2) * 1.0001f + sqrtf(P.tc_xbox2);
+        const float Rq = (sqrtf(qc2) * 1.0001f + sqrtf(P.tc_xbox2)) * P.tc_s;
         band = 2.f * tc_bound_coef<D>() * Rq * Rq;
         float thr = kTcEligible;
         // The filter value a differs from the distance by a per-query constant, so minima from
         // other node chunks prune this chunk's candidates too: every 32 tiles the running
         // minimum is published (a fire-and-forget atomicMin) and the shared one is read back,
         // to be used one period later so that the load never stalls the loop.
-        const bool pub = W.nn_amin != nullptr && qid < K;
+        const bool pub = W.nn_amin != nullptr && qid < K && !s_ovf[qrow];  // (a row out of range publishes nothing)
         unsigned gkey = 0xFFFFFFFFu;
         for (int t = 0; t < ntiles; ++t) {
             const int b = t % kTcAcc;
@@ -498,14 +477,14 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
 #pragma unroll 1
             for (int s = 0; s < np; ++s)
                 if (ring_val[s * S::READERS + e] <= thrf)
-                    tc_prefetch_group<D>(T, ring_grp[s * S::READERS + e]);
+                    tc_prefetch_group<D>(P, T, ring_grp[s * S::READERS + e]);
             float best = __int_as_float(0x7f800000);
             int bidx = 0x7FFFFFFF;
 #pragma unroll 1
             for (int s = 0; s < np; ++s) {
                 if (!(ring_val[s * S::READERS + e] <= thrf))
                     continue;
-                tc_resolve_group<D>(T, ring_grp[s * S::READERS + e], end, bound, qv, best, bidx);
+                tc_resolve_group<D>(P, T, ring_grp[s * S::READERS + e], end, bound, qv, best, bidx);
             }
             if (best < __int_as_float(0x7f800000))
                 atomicMin(&W.nn_key[qid],
@@ -608,7 +587,14 @@ cudaError_t launch_tc_pack(const DevProblem &P, Ctl *ctl, const DevTree &T, int 
 
 int tc_operand_floats(int d)
 {
-    return tc_node_cols(d);
+    return tc_node_cols(d) * kTcElem / 4;
+}
+
+float tc_scale(float xbox2)
+{
+    int e = 0;
+    std::frexp(std::sqrt((double)xbox2), &e);  // radius = m 2^e, m in [0.5, 1)
+    return (float)std::ldexp(1.0, 8 - e);      // radius * scale = m 2^8 in [2^7, 2^8)
 }
 
 }  // namespace pakr

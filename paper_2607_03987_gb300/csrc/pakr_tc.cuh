@@ -5,22 +5,26 @@
 //     a = |x - c|^2 - 2 (q - c) . (x - c)
 // with c the centre of the weighted state box.  a + |q - c|^2 is the squared
 // distance, so within one query a orders nodes like the distance.  Operands are
-// FP32 values split into TF32 parts v = hi + lo (hi = v with the low 13
-// mantissa bits cleared, lo = v - hi; the query operand truncates lo the same
-// way, the packed node copy keeps it exact so that hi + lo gives v back, and
-// the tensor core reads it as TF32); the product is formed from
-// hi.hi + hi.lo + lo.hi, and |x - c|^2 enters as hi + lo times 1.
-// One tcgen05.mma of kind::tf32 with K = 8 covers eight of those columns.
+// FP16: centred coordinates are scaled by a power of two s that brings the box
+// radius into [2^7, 2^8) (exact), and every FP32 value v is split as
+// v = hi + lo + err with hi = fp16(v), lo = fp16(v - hi) (round to nearest,
+// |err| <= 2^-22 |v| + 2^-25); the product is formed from hi.hi + hi.lo + lo.hi with
+// FP32 accumulation, and |x - c|^2 (scaled by s^2 / 2^8) enters as hi + lo times
+// 2^8.  One tcgen05.mma of kind::f16 with K = 16 covers sixteen of those columns.
+// FP16 has TF32's 11-bit significand, so the split is as precise as a TF32 one, at
+// twice the columns per MMA and half the operand bytes.
 //
 // Two layouts of the packed node row (TcShape<D>::SPLIT chooses):
-//  - split (d = 3, 5, 6): the row is (x_hi, x_lo, |x|^2 hi, lo) in 2d + 2 columns rounded up
-//    to 8, and the query has two operands: (-2q_hi against x_hi and x_lo, 1, 1) over the whole
-//    row, and (-2q_lo) against the x_hi columns alone, issued as extra MMAs into the same
-//    accumulator.  No column is stored twice;
-//  - joint (other d): the row is (x_hi, x_lo, x_hi, |x|^2 hi, lo) in 3d + 2 columns rounded
-//    up to 8 against one query operand (-2q_hi, -2q_hi, -2q_lo, 1, 1).  Used where the split
-//    form would need more MMAs per tile (d = 12: 6 instead of 5) or save no bytes (d = 4).
+//  - split (d = 5, 6, 12): the row is (x_hi, x_lo, |x|^2 hi, lo) in 2d + 2 columns rounded
+//    up to 16, and the query has two operands: (-2q_hi against x_hi and x_lo, 2^8, 2^8)
+//    over the whole row, and (-2q_lo) against the x_hi columns alone, issued as extra MMAs
+//    into the same accumulator.  No column is stored twice;
+//  - joint (d = 3, 4): the row is (x_hi, x_lo, x_hi, |x|^2 hi, lo) in 3d + 2 columns
+//    rounded up to 16 against one query operand (-2q_hi, -2q_hi, -2q_lo, 2^8, 2^8): one MMA
+//    per tile, where the split form would take two.
 #pragma once
+#include <cuda_fp16.h>
+
 #include "pakr_internal.h"
 
 namespace pakr {
@@ -122,21 +126,21 @@ __device__ __forceinline__ bool mbar_wait_suspend(uint32_t bar, uint32_t parity,
             return false;
     }
 }
-// D[tmem] (+)= A[smem] * B[smem]^T, kind::tf32, one CTA; the accumulate flag ACC is fixed at
-// compile time (no predicate computed per MMA).
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (FP16 operands, FP32 accumulator), one CTA;
+// the accumulate flag ACC is fixed at compile time (no predicate computed per MMA).
 template <bool ACC>
-__device__ __forceinline__ void mma_tf32_ss_c(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc)
+__device__ __forceinline__ void mma_f16_ss_c(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc)
 {
     if constexpr (ACC)
         asm volatile("{\n\t.reg .pred p;\n\t"
                      "setp.eq.u32 p, 1, 1;\n\t"
-                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
                      "l"(adesc), "l"(bdesc), "r"(idesc)
                      : "memory");
     else
         asm volatile("{\n\t.reg .pred p;\n\t"
                      "setp.eq.u32 p, 1, 0;\n\t"
-                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
                      "l"(adesc), "l"(bdesc), "r"(idesc)
                      : "memory");
 }
@@ -184,15 +188,19 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
-// Instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
+// Instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A and B f16 (type code 0), both
+// K-major, N / 8 at bit 17, M / 16 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N)
 {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // ---------------------------------------------------------------------------
 // Operand geometry.
 // ---------------------------------------------------------------------------
+constexpr int kTcElem = 2;        // bytes per operand element (FP16)
+constexpr int kTcKStep = 16;      // K of one MMA (32 bytes of a row)
+constexpr int kTcCoreK = 8;       // elements per 16-byte core-matrix row
 constexpr int kTcM = 128;        // queries per CTA (MMA M)
 constexpr int kTcN = 256;        // nodes per tile of the packed operand copy
 constexpr int kTcBN = 128;       // nodes per pipeline stage and MMA (N): half a packed tile
@@ -200,8 +208,14 @@ constexpr int kTcAcc = 4 / kTcCtasPerSm;  // accumulators of kTcBN columns per C
 constexpr int kTcCols = kTcAcc * kTcBN;  // TMEM columns per CTA
 constexpr int kTcG = 16;         // nodes per filter group
 constexpr int kTcRing = 8;       // candidate groups remembered per (query, reader)
-constexpr float kTcSentinel = 1.2676506e30f;  // 2^100: |x - c|^2 of ineligible and padding nodes
-constexpr float kTcEligible = 6.338253e29f;   // 2^99: filter values at or above are not eligible nodes
+// Scaled units (box radius X in [2^7, 2^8), queries within 2^9 of the centre): real filter
+// values are below X^2 + 2 |2q| X < 2^19.  Ineligible and padding nodes get 2^15 in the
+// |x - c|^2 hi column, 2^23 after the query's 2^8, and filter values at or above 2^22 are
+// not eligible nodes.
+constexpr float kTcSentinel = 32768.f;
+constexpr float kTcEligible = 4194304.f;
+constexpr float kTcNormA = 256.f;     // query operand's |x - c|^2 columns (the node's are scaled by 2^-8)
+constexpr float kTcQueryMax2 = 262144.f;  // (2^9)^2: farther queries are rescanned exactly
 // warp roles
 constexpr int kTcLoadWarp = 0;   // lane 0: bulk copies of node half tiles and f-costs
 constexpr int kTcMmaWarp = 1;    // lane 0: MMAs; the warp owns the TMEM allocation
@@ -209,12 +223,13 @@ constexpr int kTcPatch0 = 2;     // warps 2-3: mask ineligible rows, signal "sta
 constexpr int kTcReader0 = 4;    // warps 4 and up: accumulator readers (warp w reads lane quarter w % 4)
 
 // Columns of the packed node row for state dimension d (see the two layouts above).
-__host__ __device__ constexpr int tc_cols_joint(int d) { return ((3 * d + 2) + 7) / 8 * 8; }
-__host__ __device__ constexpr int tc_cols_split(int d) { return ((2 * d + 2) + 7) / 8 * 8; }
+__host__ __device__ constexpr int tc_round_k(int c) { return (c + kTcKStep - 1) / kTcKStep * kTcKStep; }
+__host__ __device__ constexpr int tc_cols_joint(int d) { return tc_round_k(3 * d + 2); }
+__host__ __device__ constexpr int tc_cols_split(int d) { return tc_round_k(2 * d + 2); }
 __host__ __device__ constexpr bool tc_split(int d)
 {
     return tc_cols_split(d) < tc_cols_joint(d) &&
-           tc_cols_split(d) / 8 + (d + 7) / 8 <= tc_cols_joint(d) / 8;
+           tc_cols_split(d) / kTcKStep + tc_round_k(d) / kTcKStep <= tc_cols_joint(d) / kTcKStep;
 }
 __host__ __device__ constexpr int tc_node_cols(int d) { return tc_split(d) ? tc_cols_split(d) : tc_cols_joint(d); }
 
@@ -222,15 +237,15 @@ template <int D>
 struct TcShape {
     static constexpr bool SPLIT = tc_split(D);
     static constexpr int KT = tc_node_cols(D);                 // columns of a packed node row
-    static constexpr int KA2 = SPLIT ? (D + 7) / 8 * 8 : 0;    // columns of the second query operand
+    static constexpr int KA2 = SPLIT ? tc_round_k(D) : 0;      // columns of the second query operand
     static constexpr int NORM = SPLIT ? 2 * D : 3 * D;         // column of |x|^2 hi (lo follows)
-    static constexpr int MMAS = KT / 8 + KA2 / 8;              // MMAs of K = 8 per stage
-    static constexpr int LBO = 128, SBO = KT * 32;             // no-swizzle K-major core-matrix layout
-    static constexpr int SBO2 = KA2 * 32;                      // the same for the second query operand
-    static constexpr int TILE_BYTES = kTcN * KT * 4;           // one packed node tile, contiguous
-    static constexpr int STAGE_BYTES = kTcBN * KT * 4;         // half a packed tile: also contiguous
-    static constexpr int A1_BYTES = kTcM * KT * 4;
-    static constexpr int A_BYTES = A1_BYTES + kTcM * KA2 * 4;
+    static constexpr int MMAS = (KT + KA2) / kTcKStep;         // MMAs per stage
+    static constexpr int LBO = 128, SBO = KT * kTcElem * 8;    // no-swizzle K-major core-matrix layout
+    static constexpr int SBO2 = KA2 * kTcElem * 8;             // the same for the second query operand
+    static constexpr int TILE_BYTES = kTcN * KT * kTcElem;     // one packed node tile, contiguous
+    static constexpr int STAGE_BYTES = kTcBN * KT * kTcElem;   // half a packed tile: also contiguous
+    static constexpr int A1_BYTES = kTcM * KT * kTcElem;
+    static constexpr int A_BYTES = A1_BYTES + kTcM * KA2 * kTcElem;
     static constexpr int F_BYTES = kTcBN * 4;
     // reader warps per TMEM lane quarter: two (64 accumulator columns each) for d <= 8, one
     // (all 128) for larger d, whose resolve needs the registers (measured both ways: d = 6
@@ -241,48 +256,70 @@ struct TcShape {
     static constexpr int RING_BYTES = kTcRing * READERS * 8;
     // two CTAs per SM: each within half of the SM's 228 KB, static shared memory included
     static constexpr int NSTAGE_FIT = (100 * 1024 - A_BYTES - RING_BYTES) / (STAGE_BYTES + F_BYTES);
-    static constexpr int NSTAGE = NSTAGE_FIT > 8 ? 8 : NSTAGE_FIT;  // half tiles staged in shared memory
+    static constexpr int NSTAGE = NSTAGE_FIT > 16 ? 16 : NSTAGE_FIT;  // half tiles staged in shared memory
     static constexpr int SMEM = A_BYTES + NSTAGE * (STAGE_BYTES + F_BYTES) + RING_BYTES;
     // and at least enough that no third CTA fits beside them (two CTAs take all 512 TMEM columns)
     static constexpr int SMEM_REQ = SMEM > 80 * 1024 ? SMEM : 80 * 1024;
-    static_assert(NSTAGE >= 2, "shared memory stages");
+    static_assert(NSTAGE >= 2 && NSTAGE >= kTcAcc, "shared memory stages");
 };
 
 // Byte offset of (row r, column k) in a no-swizzle K-major tile with KT columns.
 template <int D>
 __host__ __device__ __forceinline__ uint32_t tc_off(int r, int k)
 {
-    return (uint32_t)((r >> 3) * TcShape<D>::SBO + (k >> 2) * TcShape<D>::LBO + (r & 7) * 16 + (k & 3) * 4);
+    return (uint32_t)((r >> 3) * TcShape<D>::SBO + (k / kTcCoreK) * TcShape<D>::LBO + (r & 7) * 16 +
+                      (k % kTcCoreK) * kTcElem);
 }
 // The same in the second query operand (KA2 columns).
 template <int D>
 __host__ __device__ __forceinline__ uint32_t tc_off2(int r, int k)
 {
-    return (uint32_t)((r >> 3) * TcShape<D>::SBO2 + (k >> 2) * TcShape<D>::LBO + (r & 7) * 16 + (k & 3) * 4);
+    return (uint32_t)((r >> 3) * TcShape<D>::SBO2 + (k / kTcCoreK) * TcShape<D>::LBO + (r & 7) * 16 +
+                      (k % kTcCoreK) * kTcElem);
 }
 
-__device__ __forceinline__ float tf32_trunc(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+__device__ __forceinline__ float f16_round(float v) { return __half2float(__float2half_rn(v)); }
+// One 16-byte core-matrix row of kTcCoreK consecutive columns, from floats FP16 holds exactly.
+__device__ __forceinline__ uint4 tc_chunk(const float *v)
+{
+    const __half2 h0 = __floats2half2_rn(v[0], v[1]), h1 = __floats2half2_rn(v[2], v[3]);
+    const __half2 h2 = __floats2half2_rn(v[4], v[5]), h3 = __floats2half2_rn(v[6], v[7]);
+    return make_uint4(*reinterpret_cast<const uint32_t *>(&h0), *reinterpret_cast<const uint32_t *>(&h1),
+                      *reinterpret_cast<const uint32_t *>(&h2), *reinterpret_cast<const uint32_t *>(&h3));
+}
+__device__ __forceinline__ void tc_store_elem(unsigned char *p, float v) { *reinterpret_cast<__half *>(p) = __float2half_rn(v); }
+// v = hi + lo + err in FP16 (|v| well inside its range): round to nearest twice, |err| <=
+// 2^-22 |v| + 2^-25 (the second term where lo is subnormal).  v - hi is exact in FP32.
+__device__ __forceinline__ void tc_split_val(float v, float &hi, float &lo)
+{
+    hi = f16_round(v);
+    lo = f16_round(v - hi);
+}
 
 // Bound on |a + |q - c|^2 - e| relative to R^2 = (|q - c| + X)^2, with e the exact FP32
-// squared distance the result is defined by and X the bound on |x - c| over the state box.
-// Terms (u = 2^-24): the hi/lo truncations leave |v - hi - lo| < 2^-20 |v| per operand, so
-// the three partial products miss -2 q.x by at most 6 2^-20 |q||x| <= 1.5 2^-20 R^2, and
-// |x|^2 by 2^-20 |x|^2; FP32 |x - c|^2 adds gamma_d; the exact form e carries gamma_(d+2);
-// rounding x - c and q - c moves the distance by at most 2.01 u R^2; the tensor-core
-// accumulation is taken as 4 (KT/8 + 1) u of the sum of |products| (measured on this GPU
-// at most 5.2 u with 5 accumulating k-steps, 2.2 u with one; taken per MMA of the stage,
-// whichever operand it reads).  The total is doubled.
+// squared distance the result is defined by and X the bound on |x - c| over the state box,
+// all in the scaled coordinates (X >= 2^7; scaling by a power of two commutes with FP32
+// rounding).  Terms (u = 2^-24): the split leaves |v - hi - lo| <= 2^-22 |v| + 2^-25 per
+// operand, so the three partial products miss -2 q.x by at most 3.01 2^-22 |2q||x| <=
+// 1.505 2^-22 R^2 (|q||x| <= R^2 / 4), and |x|^2 by 2^-22 |x|^2 <= 2^-22 R^2; the subnormal
+// floor adds 2^-25 (|2q|_1 + |x|_1) + 2^-25 2^8 (the norm's), below 0.05 u R^2 once X >= 2^7;
+// FP32 |x - c|^2 adds gamma_d; the exact form e carries gamma_(d+2); rounding x - c and
+// q - c moves the distance by at most 2.01 u R^2; the tensor-core accumulation is taken as
+// 4 (MMAS + 1) u of the sum of |products|, which is at most R^2 (measured on this GPU: at most
+// 6.1 u with 4 accumulating FP16 k-steps).  The total is doubled.
 template <int D>
 __host__ __device__ constexpr float tc_bound_coef()
 {
     constexpr float u = 5.9604645e-8f;
     constexpr int MMAS = TcShape<D>::MMAS;
-    return 2.f * (2.5f * 16.f * u + D * u / (1.f - D * u) + (D + 2) * u / (1.f - (D + 2) * u) +
+    return 2.f * (2.51f * 4.f * u + 0.05f * u + D * u / (1.f - D * u) + (D + 2) * u / (1.f - (D + 2) * u) +
                   1.01f * 4.f * (MMAS + 1) * u + 2.01f * u);
 }
 
-// Write node j's packed operand row (state x, unweighted) into the tree's tile copy;
-// flag the tree when |x_w - c|^2 exceeds the box bound the error analysis assumes.
+// Write node j's packed operand row (state x, unweighted) into the tree's tile copy: the
+// centred coordinates scaled by P.tc_s and |x - c|^2 by P.tc_s^2 / 2^8 (powers of two,
+// exact), each split into FP16 hi + lo.  Flag the tree when |x_w - c|^2 exceeds the box
+// bound the error analysis assumes (its searches then rescan exactly).
 template <int D>
 __device__ __forceinline__ void tc_pack_node(const DevProblem &P, const DevTree &T, Ctl *ctl, int j, const float *x)
 {
@@ -290,32 +327,37 @@ __device__ __forceinline__ void tc_pack_node(const DevProblem &P, const DevTree 
         return;
     using S = TcShape<D>;
     constexpr int KT = S::KT;
-    float row[KT];
+    float row[KT], v[D];
 #pragma unroll
     for (int k = 0; k < KT; ++k)
         row[k] = 0.f;
     float xn = 0.f;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        const float v = x[a] * P.sw[a] - P.tc_c[a];
-        xn = __fmaf_rn(v, v, xn);
-        const float hi = tf32_trunc(v);
-        row[a] = hi;
-        row[D + a] = v - hi;  // exact; the tensor core reads it as TF32, the exact resolve adds it to hi
-        if constexpr (!S::SPLIT)
-            row[2 * D + a] = hi;
+        v[a] = x[a] * P.sw[a] - P.tc_c[a];
+        xn = __fmaf_rn(v[a], v[a], xn);
     }
-    const float nh = tf32_trunc(xn);
-    row[S::NORM] = nh;
-    row[S::NORM + 1] = tf32_trunc(xn - nh);
-    if (!(xn <= P.tc_xbox2))
+    // a node outside the box bound keeps a zero row: its scaled coordinates could overflow
+    // FP16, and rows past the tree's end (of a later, smaller tree) still enter the products
+    if (xn <= P.tc_xbox2) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            float hi, lo;
+            tc_split_val(v[a] * P.tc_s, hi, lo);
+            row[a] = hi;
+            row[D + a] = lo;
+            if constexpr (!S::SPLIT)
+                row[2 * D + a] = hi;
+        }
+        tc_split_val(xn * (P.tc_s * P.tc_s / kTcNormA), row[S::NORM], row[S::NORM + 1]);
+    } else {
         atomicOr(&ctl->tc_flag, 1u);
+    }
     unsigned char *tile = reinterpret_cast<unsigned char *>(T.XT) + (size_t)(j / kTcN) * TcShape<D>::TILE_BYTES;
     const int r = j % kTcN;
 #pragma unroll
-    for (int c = 0; c < KT / 4; ++c)
-        *reinterpret_cast<float4 *>(tile + tc_off<D>(r, 4 * c)) =
-            make_float4(row[4 * c], row[4 * c + 1], row[4 * c + 2], row[4 * c + 3]);
+    for (int c = 0; c < KT / kTcCoreK; ++c)
+        *reinterpret_cast<uint4 *>(tile + tc_off<D>(r, kTcCoreK * c)) = tc_chunk(row + kTcCoreK * c);
 }
 
 }  // namespace pakr

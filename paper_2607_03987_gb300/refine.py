@@ -93,8 +93,9 @@ def traj_check(planner, controls, x0, x_goal):
 
 def expand_controls(edge_controls, steps):
     """Per-step controls of a path: edge e's control repeated steps[e] times."""
-    reps = torch.as_tensor(np.asarray(steps), dtype=torch.long, device=edge_controls.device)
-    return torch.repeat_interleave(edge_controls, reps, dim=0)
+    steps = np.asarray(steps)
+    reps = torch.as_tensor(steps, dtype=torch.long, device=edge_controls.device)
+    return torch.repeat_interleave(edge_controls, reps, dim=0, output_size=int(steps.sum()))
 
 
 def refine_path(planner, spec, path, x_goal, iters=15, candidates=16, step=0.5, weights=None):
@@ -126,8 +127,10 @@ def refine_path(planner, spec, path, x_goal, iters=15, candidates=16, step=0.5, 
     xc = x0.expand(candidates, -1).contiguous()
     inf = torch.tensor(float("inf"), device=dev)
 
+    n_steps = int(steps.sum())  # given to repeat_interleave, which would otherwise read it back from the device
+
     def per_step(uu):
-        return torch.repeat_interleave(uu, reps, dim=-2)
+        return torch.repeat_interleave(uu, reps, dim=-2, output_size=n_steps)
 
     # a shortened path tends to end on the goal sphere itself; it is accepted only with its end
     # inside the ball by a relative margin, so that replaying it in another precision stays in
@@ -264,7 +267,7 @@ def refined_aox_concurrent(planner, ref_planner, spec, budget_s, seed=0, refine_
 
 
 def refined_aox_live(planner, ref_planner, spec, budget_s, seed=0, refine_iters=15, max_edges=1024,
-                     poll_s=0.0005):
+                     poll_s=0.0005, stats=None):
     """One AO-x run with refinement beside it for its whole budget.
 
     The device AO-x loop runs once, as pakr_plan with this seed would (the same graph, the same
@@ -275,7 +278,9 @@ def refined_aox_live(planner, ref_planner, spec, budget_s, seed=0, refine_iters=
     shorter than everything so far is offered to the running loop as its bound
     (pakr_plan_offer_bound).  Until the first offer lands the loop does exactly what
     plain AO-x does; after it, it prunes against the tighter bound.  Returns (best cost,
-    total refinement gain, best path as dict(x0, controls, steps) or None)."""
+    total refinement gain, best path as dict(x0, controls, steps) or None).  A dict passed as
+    `stats` receives the number of refinements run and improving, their durations and the time
+    the first path was seen."""
     import threading
 
     d, m = spec["d"], spec["m"]
@@ -306,6 +311,8 @@ def refined_aox_live(planner, ref_planner, spec, budget_s, seed=0, refine_iters=
             inf_h = info.cpu().numpy()
         if inf_h[0] == 1 and int(inf_h[2]) > seen and time.perf_counter() - t0 + t_refine < budget_s:
             t_start = time.perf_counter()
+            if stats is not None and "first_path_s" not in stats:
+                stats["first_path_s"] = t_start - t0
             seen = int(inf_h[2])
             ne = int(inf_h[1])
             c = float(np.array([inf_h[3]], dtype=np.int32).view(np.float32)[0])
@@ -313,7 +320,11 @@ def refined_aox_live(planner, ref_planner, spec, budget_s, seed=0, refine_iters=
                 path = dict(x0=st[0].cpu().numpy(), controls=ct[:ne].cpu().numpy(), steps=sp[:ne].cpu().numpy())
                 ref = refine_path(ref_planner, spec, path, spec["x_goal"], iters=refine_iters)
                 base = min(c, best_ref)
+                if stats is not None:
+                    stats["refined"] = stats.get("refined", 0) + 1
                 if ref is not None and ref[1] < base:
+                    if stats is not None:
+                        stats["improved"] = stats.get("improved", 0) + 1
                     gain += base - ref[1]
                     best_ref = ref[1]
                     best_path = dict(x0=path["x0"], controls=ref[0].detach().cpu().numpy(), steps=path["steps"])
@@ -321,6 +332,8 @@ def refined_aox_live(planner, ref_planner, spec, budget_s, seed=0, refine_iters=
                     planner.offer_bound(cost_dev, side)
             side.synchronize()
             t_refine = time.perf_counter() - t_start
+            if stats is not None:
+                stats.setdefault("refine_s", []).append(t_refine)
         else:
             time.sleep(poll_s)
     th.join()
