@@ -541,7 +541,8 @@ def refined_vs_plain(dev, stream, budget_s=0.1, seeds=10, n_boxes=50):
     from paper_2607_03987_gb300 import workloads as W
 
     spec = W.problem("di3", env_seed=0, n_boxes=n_boxes)
-    s_plan, s_side = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    # the refinement's stream at high priority: its kernel takes the next free SM slot
+    s_plan, s_side = torch.cuda.Stream(dev), torch.cuda.Stream(dev, priority=-1)
     planner = pakr.Planner(spec, device=dev, stream=s_plan)
     ref_planner = pakr.Planner(W.with_sizes(spec, K=1, k=1, cap=16), device=dev, stream=s_side)
     refine.refined_aox_live(planner, ref_planner, spec, 0.05, seed=999)  # warm-up (graphs, torch kernels)

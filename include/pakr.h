@@ -462,6 +462,38 @@ pakr_status pakr_traj_check(pakr_planner *planner, const float *x0, const float 
                             int32_t n_steps, const float *x_goal, int32_t *valid, int32_t *in_goal,
                             float *path_length, float *x_final);
 
+/* Refinement of one path by projected gradient steps on its per-edge controls,
+ * in one kernel launch (a 64-thread CTA, small enough to run beside the
+ * search kernels of a plan on another stream).  A refinement step of the
+ * AO-x solutions, not a step of the paper's method.
+ *   x0             device, d floats: the path's start state;
+ *   edge_controls  device, n_edges x m floats, row-major: the control of each
+ *                  edge, updated in place when a shorter path is accepted;
+ *   steps          device, n_edges int32: RK4 steps of each edge, summing to
+ *                  n_steps (the step counts stay fixed);
+ *   x_goal         host, d floats; params: the smooth cost whose gradient
+ *                  gives the descent direction (as pakr_traj_cost);
+ *   iters          iterations; each takes the gradient of the cost with
+ *                  respect to the edge controls, normalises it to d, tries the
+ *                  n_candidates (1..32) candidates clamp(u - step 2^-c d,
+ *                  u_lo, u_hi), c = 0, 1, ..., and keeps the shortest one (the
+ *                  lowest c on a tie) that the planner's rules accept (valid
+ *                  after every step as pakr_traj_check, the end in the goal
+ *                  ball and within goal_radius * (1 - goal_margin) of the
+ *                  goal), if it is shorter than the current path;
+ *   scratch        device, pakr_traj_refine_scratch_floats floats, caller-owned;
+ *   lengths        device, 2 floats: the starting path length (+inf if the
+ *                  start is not accepted) and the final one; both NaN if the
+ *                  step counts are negative or do not sum to n_steps.
+ * Enqueues on the planner's stream; nothing is read back to the host. */
+pakr_status pakr_traj_refine(pakr_planner *planner, const float *x0, float *edge_controls, const int32_t *steps,
+                             int32_t n_edges, int32_t n_steps, const float *x_goal, const pakr_traj_params *params,
+                             int32_t iters, int32_t n_candidates, float step, float goal_margin, float *scratch,
+                             float *lengths);
+
+/* Size in floats of the scratch pakr_traj_refine needs (-1 on a bad argument). */
+int64_t pakr_traj_refine_scratch_floats(const pakr_planner *planner, int32_t n_edges, int32_t n_steps);
+
 /* Cost-pruned nearest neighbour that allocates no device memory.
  *
  * The paper has no counterpart of this call: it exists for callers that

@@ -25,6 +25,8 @@ namespace {
 
 constexpr int kCkpt = 16;  // checkpoint interval of the adjoint sweep
 constexpr int kTrajWarpsPerBlock = 4;
+constexpr int kRefineWarps = 2;     // warps of the refinement CTA: it fits beside the search kernels on an SM
+constexpr int kRefineMaxCand = 32;  // line-search candidates per refinement iteration at most
 
 struct TrajWeights {
     float w_dur, w_u, w_obs, beta, margin, w_goal, w_len, len_eps;
@@ -375,28 +377,22 @@ __device__ __forceinline__ void rk4_vjp(const float *x, const float *u, float h,
         ub[j] += gu[j];
 }
 
-// Gradient of the cost: a forward sweep keeps x every kCkpt steps in
-// ckpt (one row of kMaxCkpt per trajectory), then each segment is recomputed
-// from its checkpoint and the adjoint is pulled back through it.
-template <int DYN>
-__global__ void __launch_bounds__(32 * kTrajWarpsPerBlock)
-    k_traj_grad(DevProblem P, TrajWeights w, const float *__restrict__ x0, const float *__restrict__ U, int n_traj,
-                int N, const float *__restrict__ cost_grad, float *__restrict__ dU, float *__restrict__ dx0,
-                float *__restrict__ ckpt)
+// Gradient of one trajectory's cost by one warp: a forward sweep keeps x every kCkpt steps in
+// ck ((N / kCkpt + 1) rows of D), then each segment is recomputed from its checkpoint and the
+// adjoint is pulled back through it.  u_at(n, j) is control j of step n; lane 0 calls
+// grad_out(n, ub) with dJ/du_n, from the last step to the first; lam receives dJ/dx0.
+template <int DYN, class UAt, class GradOut>
+__device__ __forceinline__ void traj_adjoint_warp(const DevProblem &P, const TrajWeights &w, const float *x0, int N,
+                                                  float *ck, UAt u_at, GradOut grad_out, float *lam)
 {
     constexpr int D = Dims<DYN>::D, M = Dims<DYN>::M, PD = Dims<DYN>::PD;
-    const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (t >= n_traj)
-        return;
     const int lane = threadIdx.x & 31;
     const float h = P.dt;
     const int nseg = (N + kCkpt - 1) / kCkpt;
-    float *ck = ckpt + (size_t)t * (nseg + 1) * D;
-    const float scale = cost_grad ? cost_grad[t] : 1.f;
     float x[D], u[M], gp[3];
 #pragma unroll
     for (int a = 0; a < D; ++a)
-        x[a] = x0[(size_t)t * D + a];
+        x[a] = x0[a];
     // forward sweep: checkpoints at n = 0, 16, 32, ...
     for (int n = 0; n < N; ++n) {
         if (n % kCkpt == 0 && lane == 0) {
@@ -406,12 +402,11 @@ __global__ void __launch_bounds__(32 * kTrajWarpsPerBlock)
         }
 #pragma unroll
         for (int j = 0; j < M; ++j)
-            u[j] = U[((size_t)t * N + n) * M + j];
+            u[j] = u_at(n, j);
         rk4_step<DYN>(x, u, h, P);
     }
     __syncwarp();
     // adjoint of x_N: goal error and the obstacle penalty at x_N
-    float lam[D];
 #pragma unroll
     for (int a = 0; a < D; ++a)
         lam[a] = 0.f;
@@ -432,7 +427,7 @@ __global__ void __launch_bounds__(32 * kTrajWarpsPerBlock)
         for (int i = 0; i < L; ++i) {
 #pragma unroll
             for (int j = 0; j < M; ++j)
-                u[j] = U[((size_t)t * N + s + i) * M + j];
+                u[j] = u_at(s + i, j);
 #pragma unroll
             for (int a = 0; a < D; ++a)
                 xs[i + 1][a] = xs[i][a];
@@ -443,7 +438,7 @@ __global__ void __launch_bounds__(32 * kTrajWarpsPerBlock)
             float uu[M], ub[M], xb[D];
 #pragma unroll
             for (int j = 0; j < M; ++j) {
-                uu[j] = U[((size_t)t * N + n) * M + j];
+                uu[j] = u_at(n, j);
                 ub[j] = 2.f * w.w_u * uu[j] * h;
             }
             // path-length segment n -> n+1
@@ -458,11 +453,8 @@ __global__ void __launch_bounds__(32 * kTrajWarpsPerBlock)
             for (int a = 0; a < PD; ++a)
                 lam[a] += w.w_len * dl[a] / Ls;
             rk4_vjp<DYN>(xs[i], uu, h, P, lam, xb, ub);
-            if (lane == 0) {
-#pragma unroll
-                for (int j = 0; j < M; ++j)
-                    dU[((size_t)t * N + n) * M + j] = scale * ub[j];
-            }
+            if (lane == 0)
+                grad_out(n, ub);
 #pragma unroll
             for (int a = 0; a < D; ++a)
                 lam[a] = xb[a];
@@ -477,6 +469,34 @@ __global__ void __launch_bounds__(32 * kTrajWarpsPerBlock)
             }
         }
     }
+}
+
+// Gradient of the cost of each trajectory (one warp each), per-step controls U[(t N + n) M + j].
+template <int DYN>
+__global__ void __launch_bounds__(32 * kTrajWarpsPerBlock)
+    k_traj_grad(DevProblem P, TrajWeights w, const float *__restrict__ x0, const float *__restrict__ U, int n_traj,
+                int N, const float *__restrict__ cost_grad, float *__restrict__ dU, float *__restrict__ dx0,
+                float *__restrict__ ckpt)
+{
+    constexpr int D = Dims<DYN>::D, M = Dims<DYN>::M;
+    const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (t >= n_traj)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int nseg = (N + kCkpt - 1) / kCkpt;
+    const float scale = cost_grad ? cost_grad[t] : 1.f;
+    const float *Ut = U + (size_t)t * N * M;
+    float *dUt = dU + (size_t)t * N * M;
+    float lam[D];
+    traj_adjoint_warp<DYN>(
+        P, w, x0 + (size_t)t * D, N, ckpt + (size_t)t * (nseg + 1) * D,
+        [&](int n, int j) { return Ut[(size_t)n * M + j]; },
+        [&](int n, const float *ub) {
+#pragma unroll
+            for (int j = 0; j < M; ++j)
+                dUt[(size_t)n * M + j] = scale * ub[j];
+        },
+        lam);
     if (lane == 0 && dx0) {
 #pragma unroll
         for (int a = 0; a < D; ++a)
@@ -484,29 +504,24 @@ __global__ void __launch_bounds__(32 * kTrajWarpsPerBlock)
     }
 }
 
-// The planner's own rules on a control sequence: validity after every step,
-// the end position in the goal ball, the path length of the substep polyline.
-template <int DYN>
-__global__ void __launch_bounds__(32 * kTrajWarpsPerBlock)
-    k_traj_check(DevProblem P, TrajWeights w, const float *__restrict__ x0, const float *__restrict__ U, int n_traj,
-                 int N, int *__restrict__ valid, int *__restrict__ in_goal_out, float *__restrict__ length,
-                 float *__restrict__ x_final)
+// The planner's own rules on one control sequence, by one warp: validity after every step (in
+// the state box, no obstacle), the path length of the substep polyline, the final state in x.
+template <int DYN, class UAt>
+__device__ __forceinline__ bool traj_check_warp(const DevProblem &P, const float *x0, int N, UAt u_at, float *x,
+                                                float &len)
 {
     constexpr int D = Dims<DYN>::D, M = Dims<DYN>::M, PD = Dims<DYN>::PD;
-    const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (t >= n_traj)
-        return;
     const int lane = threadIdx.x & 31;
-    float x[D], u[M];
+    float u[M];
 #pragma unroll
     for (int a = 0; a < D; ++a)
-        x[a] = x0[(size_t)t * D + a];
+        x[a] = x0[a];
     bool ok = true;
-    float len = 0.f;
+    len = 0.f;
     for (int n = 0; n < N; ++n) {
 #pragma unroll
         for (int j = 0; j < M; ++j)
-            u[j] = U[((size_t)t * N + n) * M + j];
+            u[j] = u_at(n, j);
         float xp[PD];
 #pragma unroll
         for (int a = 0; a < PD; ++a)
@@ -522,6 +537,57 @@ __global__ void __launch_bounds__(32 * kTrajWarpsPerBlock)
         if (!inb || __any_sync(0xFFFFFFFFu, hit))
             ok = false;
     }
+    return ok;
+}
+
+// The same rules on one control sequence by one thread (the obstacle tests of a step in turn),
+// for checking one candidate per lane.
+template <int DYN, class UAt>
+__device__ __forceinline__ bool traj_check_thread(const DevProblem &P, const float *x0, int N, UAt u_at, float *x,
+                                                  float &len)
+{
+    constexpr int D = Dims<DYN>::D, M = Dims<DYN>::M, PD = Dims<DYN>::PD;
+    float u[M];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+        x[a] = x0[a];
+    bool ok = true;
+    len = 0.f;
+    for (int n = 0; n < N && ok; ++n) {
+#pragma unroll
+        for (int j = 0; j < M; ++j)
+            u[j] = u_at(n, j);
+        float xp[PD];
+#pragma unroll
+        for (int a = 0; a < PD; ++a)
+            xp[a] = x[a];
+        rk4_step<DYN>(x, u, P.dt, P);
+        len += sqrtf(sq_dist<PD>(x, xp));
+        bool inb = true;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            inb = inb && (x[a] >= P.x_lo[a]) && (x[a] <= P.x_hi[a]);
+        ok = inb && !hits_obstacle<PD>(x, P, P.boxes, P.n_boxes, P.spheres, P.n_spheres, P.grid_start, P.grid_items,
+                                       0, 1);
+    }
+    return ok;
+}
+
+template <int DYN>
+__global__ void __launch_bounds__(32 * kTrajWarpsPerBlock)
+    k_traj_check(DevProblem P, TrajWeights w, const float *__restrict__ x0, const float *__restrict__ U, int n_traj,
+                 int N, int *__restrict__ valid, int *__restrict__ in_goal_out, float *__restrict__ length,
+                 float *__restrict__ x_final)
+{
+    constexpr int D = Dims<DYN>::D, M = Dims<DYN>::M, PD = Dims<DYN>::PD;
+    const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (t >= n_traj)
+        return;
+    const int lane = threadIdx.x & 31;
+    const float *Ut = U + (size_t)t * N * M;
+    float x[D], len;
+    const bool ok =
+        traj_check_warp<DYN>(P, x0 + (size_t)t * D, N, [&](int n, int j) { return Ut[(size_t)n * M + j]; }, x, len);
     if (lane == 0) {
         valid[t] = ok ? 1 : 0;
         if (in_goal_out)
@@ -534,6 +600,123 @@ __global__ void __launch_bounds__(32 * kTrajWarpsPerBlock)
                 x_final[(size_t)t * D + a] = x[a];
         }
     }
+}
+
+// One refinement of one path, all of it on the device (one CTA of kRefineWarps warps): the
+// per-edge controls Ue (E x M, updated in place) with per-edge step counts steps[E] (summing to
+// N).  Each of `iters` iterations: warp 0 takes dJ/dUe (the adjoint sweep, per-step gradients
+// summed over each edge's steps) and normalises it to d; the warps check the n_cand candidates
+// clamp(Ue - step 2^-c d, u_lo, u_hi) under the planner's rules (valid after every step, the end
+// in the goal ball and within sqrt(r_in2) of the goal); the shortest accepted candidate (the
+// lowest c on a tie) replaces Ue if it is shorter than the current path.  Candidate c is
+// checked by thread c (kRefineMaxCand <= 32 * kRefineWarps).  out[0] receives the
+// starting length (+inf if the start is not accepted), out[1] the final one; both NaN if the
+// step counts do not sum to N.  Scratch: edge_of[N] (int), ck ((N / kCkpt + 1) x D), gE (E x M).
+template <int DYN>
+__global__ void __launch_bounds__(32 * kRefineWarps)
+    k_traj_refine(DevProblem P, TrajWeights w, const float *__restrict__ x0, float *__restrict__ Ue,
+                  const int *__restrict__ steps, int E, int N, int iters, int n_cand, float step, float r_in2,
+                  int *__restrict__ edge_of, float *__restrict__ ck, float *__restrict__ gE, float *__restrict__ out)
+{
+    constexpr int D = Dims<DYN>::D, M = Dims<DYN>::M, PD = Dims<DYN>::PD;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __shared__ float s_res[kRefineMaxCand];
+    __shared__ float s_cur;
+    __shared__ int s_ok, s_acc;
+    if (tid == 0) {
+        int n = 0;
+        bool ok = true;
+        for (int e = 0; e < E && ok; ++e) {
+            const int se = steps[e];
+            if (se < 0 || se > N - n) {
+                ok = false;
+                break;
+            }
+            for (int k = 0; k < se; ++k)
+                edge_of[n++] = e;
+        }
+        s_ok = ok && n == N;
+    }
+    __syncthreads();
+    if (!s_ok) {
+        if (tid == 0)
+            out[0] = out[1] = __int_as_float(0x7fc00000);
+        return;
+    }
+    float x0r[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+        x0r[a] = x0[a];
+    // the end rule: valid, in the goal ball, and inside it by the caller's margin; one candidate
+    // per thread
+    auto accepted_length = [&](float alpha) {
+        float x[D], len;
+        const bool ok = traj_check_thread<DYN>(
+            P, x0r, N,
+            [&](int n, int j) {
+                const int e = edge_of[n];
+                const float v = Ue[e * M + j];
+                return alpha > 0.f ? fminf(fmaxf(v - alpha * gE[e * M + j], P.u_lo[j]), P.u_hi[j]) : v;
+            },
+            x, len);
+        return (ok && in_goal<PD>(x, P, w.goal) && sq_dist<PD>(x, w.goal) <= r_in2) ? len
+                                                                                   : __int_as_float(0x7f800000);
+    };
+    if (tid == 0) {
+        const float L0 = accepted_length(0.f);
+        s_cur = L0;
+        out[0] = L0;
+    }
+    __syncthreads();
+    for (int it = 0; it < iters; ++it) {
+        if (warp == 0) {
+            for (int k = lane; k < E * M; k += 32)
+                gE[k] = 0.f;
+            __syncwarp();
+            float lam[D];
+            traj_adjoint_warp<DYN>(
+                P, w, x0r, N, ck, [&](int n, int j) { return Ue[edge_of[n] * M + j]; },
+                [&](int n, const float *ub) {
+                    const int e = edge_of[n];
+#pragma unroll
+                    for (int j = 0; j < M; ++j)
+                        gE[e * M + j] += ub[j];
+                },
+                lam);
+            __syncwarp();
+            float g2 = 0.f;
+            for (int k = lane; k < E * M; k += 32)
+                g2 = fmaf(gE[k], gE[k], g2);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                g2 += __shfl_xor_sync(0xFFFFFFFFu, g2, o);
+            const float inv = 1.f / (sqrtf(g2) + 1e-12f);
+            for (int k = lane; k < E * M; k += 32)
+                gE[k] *= inv;
+        }
+        __syncthreads();
+        if (tid < n_cand)
+            s_res[tid] = accepted_length(ldexpf(step, -tid));
+        __syncthreads();
+        if (tid == 0) {
+            int best = 0;
+            for (int c = 1; c < n_cand; ++c)
+                if (s_res[c] < s_res[best])
+                    best = c;
+            s_acc = s_res[best] < s_cur ? best : -1;
+            if (s_acc >= 0)
+                s_cur = s_res[best];
+        }
+        __syncthreads();
+        if (s_acc >= 0) {
+            const float alpha = ldexpf(step, -s_acc);
+            for (int k = tid; k < E * M; k += 32 * kRefineWarps)
+                Ue[k] = fminf(fmaxf(Ue[k] - alpha * gE[k], P.u_lo[k % M]), P.u_hi[k % M]);
+        }
+        __syncthreads();
+    }
+    if (tid == 0)
+        out[1] = s_cur;
 }
 
 #define PAKR_TRAJ_DISPATCH(dyn, BODY)                                                                                  \
@@ -683,6 +866,48 @@ pakr_status pakr_traj_check(pakr_planner *planner, const float *x0, const float 
     [&]() -> cudaError_t {
         PAKR_TRAJ_DISPATCH(P.dyn, (k_traj_check<DYN_><<<blocks, threads, 0, s>>>(
                                       P, w, x0, controls, n_traj, n_steps, valid, in_goal, path_length, x_final)));
+        return cudaSuccess;
+    }();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return tfail(PAKR_ERR_CUDA, cudaGetErrorString(e));
+    return PAKR_OK;
+}
+
+int64_t pakr_traj_refine_scratch_floats(const pakr_planner *planner, int32_t n_edges, int32_t n_steps)
+{
+    if (!planner || n_edges < 1 || n_steps < 0)
+        return -1;
+    const DevProblem &P = *planner_problem(planner);
+    const int nseg = (n_steps + kCkpt - 1) / kCkpt;
+    return (int64_t)n_steps + (int64_t)(nseg + 1) * P.d + (int64_t)n_edges * P.m;
+}
+
+pakr_status pakr_traj_refine(pakr_planner *planner, const float *x0, float *edge_controls, const int32_t *steps,
+                             int32_t n_edges, int32_t n_steps, const float *x_goal, const pakr_traj_params *params,
+                             int32_t iters, int32_t n_candidates, float step, float goal_margin, float *scratch,
+                             float *lengths)
+{
+    if (!planner || !x0 || !edge_controls || !steps || !scratch || !lengths || n_edges < 1 || n_steps < 0 ||
+        iters < 0 || n_candidates < 1 || n_candidates > kRefineMaxCand || !(step > 0.f) || !std::isfinite(step) ||
+        !(goal_margin >= 0.f && goal_margin < 1.f))
+        return tfail(PAKR_ERR_INVALID_ARG, "pakr_traj_refine: bad argument");
+    TrajWeights w;
+    pakr_status st = make_weights(planner, params, x_goal, &w);
+    if (st != PAKR_OK)
+        return st;
+    TrajGuard guard(planner_device(planner));
+    const DevProblem &P = *planner_problem(planner);
+    const float r_in = P.goal_r * (1.f - goal_margin);
+    const int nseg = (n_steps + kCkpt - 1) / kCkpt;
+    int *edge_of = reinterpret_cast<int *>(scratch);
+    float *ck = scratch + n_steps;
+    float *gE = ck + (size_t)(nseg + 1) * P.d;
+    cudaStream_t s = planner_stream(planner);
+    [&]() -> cudaError_t {
+        PAKR_TRAJ_DISPATCH(P.dyn, (k_traj_refine<DYN_><<<1, 32 * kRefineWarps, 0, s>>>(
+                                      P, w, x0, edge_controls, steps, n_edges, n_steps, iters, n_candidates, step,
+                                      r_in * r_in, edge_of, ck, gE, lengths)));
         return cudaSuccess;
     }();
     cudaError_t e = cudaGetLastError();

@@ -113,6 +113,7 @@ EXPORTED = [
     "pakr_set_profiling", "pakr_kernel_times", "pakr_philox4x32_10", "pakr_nearest_static", "pakr_version",
     "pakr_batch_create", "pakr_batch_destroy", "pakr_batch_plan", "pakr_batch_path", "pakr_batch_autotune",
     "pakr_batch_set_tuning", "pakr_traj_cost", "pakr_traj_grad", "pakr_traj_checkpoint_floats", "pakr_traj_check",
+    "pakr_traj_refine", "pakr_traj_refine_scratch_floats",
 ]
 
 _lib = None
@@ -170,11 +171,15 @@ def lib():
                                  _vp]
     L.pakr_traj_checkpoint_floats.argtypes = [_vp, C.c_int32, C.c_int32]
     L.pakr_traj_check.argtypes = [_vp, _vp, _vp, C.c_int32, C.c_int32, _PF, _vp, _vp, _vp, _vp]
+    L.pakr_traj_refine.argtypes = [_vp, _vp, _vp, _vp, C.c_int32, C.c_int32, _PF, C.POINTER(TrajParams), C.c_int32,
+                                   C.c_int32, C.c_float, C.c_float, _vp, _vp]
+    L.pakr_traj_refine_scratch_floats.argtypes = [_vp, C.c_int32, C.c_int32]
     for name in EXPORTED:
         fn = getattr(L, name)
         if name not in ("pakr_destroy", "pakr_batch_destroy", "pakr_last_error", "pakr_version"):
             fn.restype = C.c_int
     L.pakr_traj_checkpoint_floats.restype = C.c_int64
+    L.pakr_traj_refine_scratch_floats.restype = C.c_int64
     _lib = L
     return L
 

@@ -98,7 +98,12 @@ def expand_controls(edge_controls, steps):
     return torch.repeat_interleave(edge_controls, reps, dim=0, output_size=int(steps.sum()))
 
 
-def refine_path(planner, spec, path, x_goal, iters=15, candidates=16, step=0.5, weights=None):
+REFINE_WEIGHTS = dict(w_length=1.0, w_obstacle=0.05, beta=200.0, margin=0.01, w_goal=2.0, w_control=0.0,
+                      w_duration=0.0, length_eps=1e-4)
+
+
+def refine_path(planner, spec, path, x_goal, iters=15, candidates=16, step=0.5, weights=None, goal_margin=1e-4,
+                fused=True):
     """Shorten a path found by pakr_plan with its step counts fixed.
 
     Each iteration takes the gradient of the smooth cost (path length, a
@@ -106,37 +111,59 @@ def refine_path(planner, spec, path, x_goal, iters=15, candidates=16, step=0.5, 
     controls, tries `candidates` step sizes step * 2^-i along the normalised
     descent direction at once (clamped to the control box) and keeps the
     shortest candidate that the planner's rules accept (valid after every
-    substep, ending in the goal ball, here by a relative margin of 1e-4 inside it)
-    if it is shorter than the current path.
-    Everything stays on the device; the host reads the result once.  Returns
+    substep, ending in the goal ball, here by a relative margin of goal_margin
+    inside it, so that a replay in another precision stays in) if it is shorter
+    than the current path.  fused: the whole loop is one pakr_traj_refine launch
+    on the planner's stream; otherwise each iteration runs through TrajCost's
+    autograd backward and pakr_traj_check (the same rules; the per-edge gradient
+    summed in another order).  The host reads the result once.  Returns
     (controls, length), or None if no candidate improved the path."""
     dev = torch.device(f"cuda:{planner.device}")
-    steps = np.asarray(path["steps"])
+    steps = np.asarray(path["steps"], dtype=np.int32)
     if len(steps) == 0:
         return None
-    w = dict(w_length=1.0, w_obstacle=0.05, beta=200.0, margin=0.01, w_goal=2.0, w_control=0.0,
-             w_duration=0.0, length_eps=1e-4)
+    w = dict(REFINE_WEIGHTS)
     w.update(weights or {})
-    reps = torch.as_tensor(steps, dtype=torch.long, device=dev)
     x0v = path["x0"] if "x0" in path else path["states"][0]
-    x0 = torch.tensor(np.asarray(x0v, np.float32)[None], device=dev)
-    u = torch.tensor(np.asarray(path["controls"], np.float32), device=dev)
+    with torch.cuda.stream(planner.stream):
+        x0 = torch.tensor(np.asarray(x0v, np.float32)[None], device=dev)
+        u = torch.tensor(np.ascontiguousarray(np.asarray(path["controls"], np.float32)), device=dev)
+        if fused:
+            E, N = len(steps), int(steps.sum())
+            st = torch.tensor(steps, device=dev)
+            nf = int(pakr.lib().pakr_traj_refine_scratch_floats(planner.h, E, N))
+            scratch = torch.empty(max(nf, 1), dtype=torch.float32, device=dev)
+            out = torch.empty(2, dtype=torch.float32, device=dev)
+            g, gp = _goal(x_goal)
+            prm = _params(w)
+            pakr._check(pakr.lib().pakr_traj_refine(planner.h, _ptr(x0), _ptr(u), _ptr(st), E, N, gp, C.byref(prm),
+                                                    iters, candidates, step, goal_margin, _ptr(scratch), _ptr(out)),
+                        "pakr_traj_refine")
+            start_f, cur_f = (float(v) for v in out.cpu())
+        else:
+            u, cur_f, start_f = _refine_path_autograd(planner, spec, x0, u, steps, x_goal, iters, candidates, step,
+                                                      w, goal_margin)
+    if not np.isfinite(cur_f) or cur_f >= start_f:
+        return None
+    return u, cur_f
+
+
+def _refine_path_autograd(planner, spec, x0, u, steps, x_goal, iters, candidates, step, w, goal_margin):
+    dev = x0.device
+    reps = torch.as_tensor(steps, dtype=torch.long, device=dev)
     lo = torch.tensor(np.asarray(spec["u_lo"], np.float32), device=dev)
     hi = torch.tensor(np.asarray(spec["u_hi"], np.float32), device=dev)
     alphas = step * torch.pow(2.0, -torch.arange(candidates, device=dev, dtype=torch.float32))
     xc = x0.expand(candidates, -1).contiguous()
     inf = torch.tensor(float("inf"), device=dev)
-
     n_steps = int(steps.sum())  # given to repeat_interleave, which would otherwise read it back from the device
 
     def per_step(uu):
         return torch.repeat_interleave(uu, reps, dim=-2, output_size=n_steps)
 
-    # a shortened path tends to end on the goal sphere itself; it is accepted only with its end
-    # inside the ball by a relative margin, so that replaying it in another precision stays in
     pd = spec["pdim"]
     g_pos = torch.tensor(np.asarray(x_goal, np.float32)[:pd], device=dev)
-    r_in = float(spec["goal_r"]) * (1.0 - 1e-4)
+    r_in = float(spec["goal_r"]) * (1.0 - goal_margin)
 
     def inside(xf):
         return torch.linalg.norm(xf[..., :pd] - g_pos, dim=-1) <= r_in
@@ -156,10 +183,7 @@ def refine_path(planner, spec, path, x_goal, iters=15, candidates=16, step=0.5, 
         better = L[i] < cur
         u = torch.where(better, cand[i], u)
         cur = torch.where(better, L[i], cur)
-    cur_f, start_f = float(cur), float(start)
-    if not np.isfinite(cur_f) or cur_f >= start_f:
-        return None
-    return u, cur_f
+    return u, float(cur), float(start)
 
 
 def refined_aox(planner, spec, budget_s, seed=0, refine_iters=15, rounds=(0.3, 0.6, 0.85)):

@@ -168,3 +168,70 @@ def test_refine_shortens_a_found_path(cuda_lib):
     assert np.linalg.norm(x[:3] - spec["x_goal"][:3]) <= spec["goal_r"] * (1 + 1e-5)
     assert abs(total - L) <= 1e-4 * L
     planner.close()
+
+
+def test_fused_refinement_matches_autograd_loop(cuda_lib):
+    """pakr_traj_refine (the whole loop in one launch) against the same loop through TrajCost's
+    autograd backward and pakr_traj_check: the same rules and step sizes, the per-edge gradient
+    summed in another order, so after one iteration both accept a path of the same length (to
+    rounding), and after several both are accepted, valid paths."""
+    from paper_2607_03987_gb300 import refine
+
+    spec = W.problem("di3", env_seed=2)
+    planner = pakr.Planner(spec)
+    res = planner.plan(spec["x_init"], spec["x_goal"], budget_s=5.0, seed=3, stop_at_first=True)
+    assert res["n_solutions"] == 1
+    a = refine.refine_path(planner, spec, res, spec["x_goal"], iters=1, fused=True)
+    b = refine.refine_path(planner, spec, res, spec["x_goal"], iters=1, fused=False)
+    assert (a is None) == (b is None)
+    if a is not None:
+        assert abs(a[1] - b[1]) <= 1e-4 * b[1]
+    for fused in (True, False):
+        out = refine.refine_path(planner, spec, res, spec["x_goal"], iters=10, fused=fused)
+        assert out is not None
+        u, L = out
+        x = res["states"][0].astype(float)
+        total = 0.0
+        for e in range(len(res["steps"])):
+            ok, x, Le = di_replay_valid(spec, x, u[e].cpu().numpy().astype(float), int(res["steps"][e]))
+            assert ok, (fused, e)
+            total += Le
+        assert np.linalg.norm(x[:3] - spec["x_goal"][:3]) <= spec["goal_r"] * (1 + 1e-5)
+        assert abs(total - L) <= 1e-4 * L
+    planner.close()
+
+
+def test_fused_refinement_rejects_bad_step_counts(cuda_lib):
+    """Step counts that do not sum to n_steps leave the controls untouched and report NaN."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2607_03987_gb300 import refine
+
+    spec = W.problem("di3", env_seed=2)
+    planner = pakr.Planner(spec)
+    dev = torch.device("cuda:0")
+    with torch.cuda.stream(planner.stream):
+        x0 = torch.tensor(np.asarray(spec["x_init"], np.float32)[None], device=dev)
+        u = torch.zeros((3, spec["m"]), dtype=torch.float32, device=dev)
+        u0 = u.clone()
+        st = torch.tensor([2, 3, 4], dtype=torch.int32, device=dev)
+        nf = int(pakr.lib().pakr_traj_refine_scratch_floats(planner.h, 3, 10))
+        scratch = torch.empty(nf, dtype=torch.float32, device=dev)
+        out = torch.zeros(2, dtype=torch.float32, device=dev)
+        g, gp = refine._goal(spec["x_goal"])
+        prm = refine._params(refine.REFINE_WEIGHTS)
+        rc = pakr.lib().pakr_traj_refine(planner.h, C.c_void_p(x0.data_ptr()), C.c_void_p(u.data_ptr()),
+                                         C.c_void_p(st.data_ptr()), 3, 10, gp, C.byref(prm), 3, 16, 0.5, 1e-4,
+                                         C.c_void_p(scratch.data_ptr()), C.c_void_p(out.data_ptr()))
+        assert rc == 0
+        o = out.cpu().numpy()
+        assert np.all(np.isnan(o))
+        assert torch.equal(u, u0)
+        # out-of-range arguments are refused on the host
+        rc = pakr.lib().pakr_traj_refine(planner.h, C.c_void_p(x0.data_ptr()), C.c_void_p(u.data_ptr()),
+                                         C.c_void_p(st.data_ptr()), 3, 9, gp, C.byref(prm), 3, 33, 0.5, 1e-4,
+                                         C.c_void_p(scratch.data_ptr()), C.c_void_p(out.data_ptr()))
+        assert rc != 0
+    planner.close()
