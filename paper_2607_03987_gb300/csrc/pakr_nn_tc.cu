@@ -61,36 +61,6 @@ __device__ __forceinline__ float tc_exact(const DevProblem &P, const DevTree &T,
     return (f < bound) ? acc : __int_as_float(0x7f800000);
 }
 
-// Exact resolve of the 16-node group starting at g0 from the tree's own coordinates (the
-// packed FP16 copy does not hold them exactly): tc_exact per node, four nodes' loads in flight.
-template <int D>
-__device__ __forceinline__ void tc_resolve_group(const DevProblem &P, const DevTree &T, int g0, int end, float bound,
-                                                 const float *qv, float &best, int &bidx)
-{
-#pragma unroll 4
-    for (int g = 0; g < kTcG; ++g) {
-        const int j = g0 + g;
-        if (j >= end)
-            break;
-        const float ex = tc_exact<D>(P, T, j, bound, qv);
-        if (ex < best || (ex == best && j < bidx)) {
-            best = ex;
-            bidx = j;
-        }
-    }
-}
-
-// Bring the coordinates (D arrays, 64 bytes each) and f-costs of the 16-node group starting
-// at g0 into L2.
-template <int D>
-__device__ __forceinline__ void tc_prefetch_group(const DevProblem &P, const DevTree &T, int g0)
-{
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(T.X + (size_t)a * P.cap + g0));
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(T.fcost + g0));
-}
-
 // Order-preserving map of a float onto unsigned (smaller float, smaller key), so that the
 // per-query filter minimum over node chunks can use the integer atomicMin.
 __device__ __forceinline__ unsigned tc_ord(float f)
@@ -123,7 +93,7 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
     __shared__ __align__(8) unsigned long long s_done[kTcAcc], s_empty[kTcAcc], s_drain;
     __shared__ uint32_t s_tbase;
     __shared__ volatile int s_abort;
-    __shared__ int s_nflag, s_flag_qid[kTcM], s_ovf[kTcM];
+    __shared__ int s_nflag, s_nres, s_flag_qid[kTcM], s_ovf[kTcM];
     __shared__ float s_flag_q[kTcM][D];
 
     const int n = ctl->n_start;
@@ -166,6 +136,7 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
         fence_mbar_init();
         s_abort = 0;
         s_nflag = 0;
+        s_nres = 0;
     }
     if (tid < kTcM) {
         s_ovf[tid] = 0;
@@ -228,7 +199,6 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
     const int qrow = 32 * quarter + lane;
     const int e = tid - kTcReader0 * 32;  // ring column
     const int qid = qbase + qrow;
-    float qv[D];
     float m1 = kTcEligible;
     int pos = 0, ovf = 0;
     float band = 0.f;
@@ -460,41 +430,29 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
     if (s_abort)
         return;
 
-    // ---- exact resolve of the candidate groups ----
+    // ---- exact resolve of the candidate groups, by the whole CTA ----
+    // Every CTA resolves at the same moment, so the resolve is latency: the surviving (row,
+    // group) pairs go to one list, and sixteen threads take each pair, one node each, so that
+    // all the groups' loads are in flight together.  The list lives in the stages, free now
+    // (every copy has landed and every MMA has finished).
+    int2 *rlist = reinterpret_cast<int2 *>(sB0);
     if (!flagged && warp >= kTcReader0 && qid < K && (m1 < kTcEligible || s_ovf[qrow])) {
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-            qv[a] = __fsub_rn(__fmul_rn(W.xr[(size_t)a * K + qid], P.sw[a]), P.tc_c[a]);
         // against the smallest filter value any chunk has published by now (this chunk's
         // included): groups above it by more than the band cannot hold the nearest node
         const float thrf = (W.nn_amin ? fminf(m1, tc_unord(__ldcg(W.nn_amin + qid))) : m1) + band;
         // a row either of whose readers lost a candidate is rescanned instead (once)
         if (!s_ovf[qrow]) {
-            // every CTA resolves at the same moment, and the streamed tiles have mostly left
-            // L2 by now: request all surviving groups' lines first, so that their DRAM round
-            // trips overlap instead of following one another group by group
             const int np = min(pos, kTcRing);
 #pragma unroll 1
             for (int s = 0; s < np; ++s)
                 if (ring_val[s * S::READERS + e] <= thrf)
-                    tc_prefetch_group<D>(P, T, ring_grp[s * S::READERS + e]);
-            float best = __int_as_float(0x7f800000);
-            int bidx = 0x7FFFFFFF;
-#pragma unroll 1
-            for (int s = 0; s < np; ++s) {
-                if (!(ring_val[s * S::READERS + e] <= thrf))
-                    continue;
-                tc_resolve_group<D>(P, T, ring_grp[s * S::READERS + e], end, bound, qv, best, bidx);
-            }
-            if (best < __int_as_float(0x7f800000))
-                atomicMin(&W.nn_key[qid],
-                          ((unsigned long long)__float_as_uint(best) << 32) | (unsigned long long)(uint32_t)bidx);
+                    rlist[atomicAdd(&s_nres, 1)] = make_int2(qrow, ring_grp[s * S::READERS + e]);
         } else if (half == 0) {
             const int slot = atomicAdd(&s_nflag, 1);
             s_flag_qid[slot] = qid;
 #pragma unroll
             for (int a = 0; a < D; ++a)
-                s_flag_q[slot][a] = qv[a];
+                s_flag_q[slot][a] = __fsub_rn(__fmul_rn(W.xr[(size_t)a * K + qid], P.sw[a]), P.tc_c[a]);
         }
     }
     if (flagged && tid < kTcM) {
@@ -509,6 +467,38 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
         }
     }
     __syncthreads();
+    {
+        // sixteen threads per (row, group), node g0 + k for thread k; the two halves of a warp take
+        // neighbouring pairs and run the same trips, so that the shuffles stay warp-uniform
+        const int nres = s_nres;
+        const int sub = lane & (kTcG - 1);
+        for (int base = 2 * warp; base < nres; base += S::THREADS / kTcG) {
+            const int it = base + (lane >> 4);
+            unsigned long long key = kNoKey;
+            int q = 0;
+            if (it < nres) {
+                const int2 item = rlist[it];
+                q = qbase + item.x;
+                const int j = item.y + sub;
+                if (j < end) {
+                    float qv2[D];
+#pragma unroll
+                    for (int a = 0; a < D; ++a)
+                        qv2[a] = __fsub_rn(__fmul_rn(W.xr[(size_t)a * K + q], P.sw[a]), P.tc_c[a]);
+                    const float ed = tc_exact<D>(P, T, j, bound, qv2);
+                    if (ed < __int_as_float(0x7f800000))
+                        key = ((unsigned long long)__float_as_uint(ed) << 32) | (unsigned long long)(uint32_t)j;
+                }
+            }
+#pragma unroll
+            for (int o = kTcG / 2; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, key, o);
+                key = other < key ? other : key;
+            }
+            if (sub == 0 && key != kNoKey)
+                atomicMin(&W.nn_key[q], key);
+        }
+    }
     // exact rescans of the flagged queries by the whole block (coalesced nodes, warp minimum of packed keys)
     const int nflag = s_nflag;
     for (int f = 0; f < nflag; ++f) {

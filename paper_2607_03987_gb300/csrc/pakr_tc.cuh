@@ -261,6 +261,8 @@ struct TcShape {
     // and at least enough that no third CTA fits beside them (two CTAs take all 512 TMEM columns)
     static constexpr int SMEM_REQ = SMEM > 80 * 1024 ? SMEM : 80 * 1024;
     static_assert(NSTAGE >= 2 && NSTAGE >= kTcAcc, "shared memory stages");
+    // after the tile loop the stages hold the resolve list: one (row, group) pair per ring entry
+    static_assert(NSTAGE * STAGE_BYTES >= kTcRing * READERS * 8, "resolve list in the stages");
 };
 
 // Byte offset of (row r, column k) in a no-swizzle K-major tile with KT columns.
