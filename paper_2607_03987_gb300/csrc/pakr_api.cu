@@ -343,11 +343,15 @@ struct pakr_planner {
     int path_cap = 0, hist_cap = 0;
     cudaGraphExec_t plan_exec = nullptr;
     cudaGraph_t plan_graph = nullptr;
-    // one expansion as a graph (pakr_expand without profiling): its sample node takes
-    // the bound and seed of each call
-    cudaGraphExec_t expand_exec = nullptr;
-    cudaGraph_t expand_graph = nullptr;
-    cudaGraphNode_t expand_sample = nullptr;
+    // one expansion as a graph (pakr_expand without profiling), one per nearest-neighbour
+    // kernel ([0] k_nn, [1] k_nn_tc): its sample node takes the bound and seed of each call
+    cudaGraphExec_t expand_exec[2] = {nullptr, nullptr};
+    cudaGraph_t expand_graph[2] = {nullptr, nullptr};
+    cudaGraphNode_t expand_sample[2] = {nullptr, nullptr};
+    // an upper bound on the device-side tree size, for choosing the nearest-neighbour kernel
+    // on the host: exact after every read of the control block and every host-side tree
+    // operation, raised by K * k per expansion in between
+    int64_t n_upper = 0;
     // profiling
     bool profiling = false;
     std::vector<EventPair> pool;
@@ -405,24 +409,37 @@ pakr_status timed(pakr_planner *p, int slot, F &&launch, const char *what)
     return PAKR_OK;
 }
 
-pakr_status enqueue_expand(pakr_planner *p, float bound, uint64_t seed)
+// The nearest-neighbour kernel for the next expansion, chosen on the host: the tensor-core one
+// once the tree can hold tc_min_n nodes (by the upper bound; either kernel gives the same
+// result at any size, the choice only decides the speed).
+bool use_tc_nn(const pakr_planner *p)
+{
+    return p->T.XT != nullptr && p->P.tc_min_n < 0x7FFFFFFF && p->n_upper >= p->P.tc_min_n;
+}
+
+// P for a nearest-neighbour kernel launched for any tree size (its device-side range check
+// then always passes).
+DevProblem nn_problem(const pakr_planner *p, bool tc)
+{
+    DevProblem P = p->P;
+    P.tc_min_n = tc ? 0 : 0x7FFFFFFF;
+    return P;
+}
+
+pakr_status enqueue_expand(pakr_planner *p, float bound, uint64_t seed, bool tc)
 {
     pakr_status st;
     st = timed(p, 0, [&] { return launch_sample(p->P, p->ctl, p->W, p->L, bound, seed, MODE_EXPAND, p->stream); },
                "sample");
     if (st != PAKR_OK)
         return st;
-    // both nearest-neighbour kernels; each returns at once unless the tree size is its range
-    if (p->P.tc_min_n > 0) {
-        st = timed(p, 1, [&] { return launch_nn_fp32(p->P, p->ctl, p->T, p->W, p->L, p->stream); }, "nearest");
-        if (st != PAKR_OK)
-            return st;
-    }
-    if (p->T.XT && p->P.tc_min_n < 0x7FFFFFFF) {
-        st = timed(p, 4, [&] { return launch_nn_tc(p->P, p->ctl, p->T, p->W, p->L, p->stream); }, "nearest (tc)");
-        if (st != PAKR_OK)
-            return st;
-    }
+    const DevProblem Pn = nn_problem(p, tc);
+    if (tc)
+        st = timed(p, 4, [&] { return launch_nn_tc(Pn, p->ctl, p->T, p->W, p->L, p->stream); }, "nearest (tc)");
+    else
+        st = timed(p, 1, [&] { return launch_nn_fp32(Pn, p->ctl, p->T, p->W, p->L, p->stream); }, "nearest");
+    if (st != PAKR_OK)
+        return st;
     st = timed(p, 2, [&] { return launch_propagate(p->P, p->ctl, p->T, p->W, p->L, p->stream); }, "propagate");
     if (st != PAKR_OK)
         return st;
@@ -467,57 +484,28 @@ pakr_status capture_one(pakr_planner *p, cudaGraph_t g, cudaGraphNode_t dep, F &
     return PAKR_OK;
 }
 
-// An IF node on handle h after `dep`, whose body holds the one launch `launch`.
-template <class F>
-pakr_status add_if(pakr_planner *p, cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle h, F &&launch,
-                   cudaGraphNode_t *node)
-{
-    cudaGraphNodeParams cp{};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeIf;
-    cp.conditional.size = 1;
-    CUDA_TRY(cudaGraphAddNode(node, g, &dep, nullptr, 1, &cp));
-    cudaGraphNode_t inner = nullptr;
-    return capture_one(p, cp.conditional.phGraph_out[0], nullptr, launch, &inner);
-}
-
 // Which nearest-neighbour kernel an expansion graph runs.
-enum NnKind { NN_SELECT = 0, NN_ONLY_FP32 = 1, NN_ONLY_TC = 2 };
+enum NnKind { NN_ONLY_FP32 = 1, NN_ONLY_TC = 2 };
 
-// Append one expansion to graph g after `dep`: sample, nearest neighbour, propagate,
-// append.  NN_SELECT with the packed tree copy puts k_nn and k_nn_tc in IF nodes that
-// k_sample opens one of; otherwise the one kernel runs as a plain node.
+// Append one expansion to graph g after `dep`: sample, nearest neighbour (the one kernel of
+// `kind`, launched for any tree size: the graph's owner has chosen it), propagate, append.
+// No conditional node: a device-side IF node costs about 10 us of the step on GB300.
 pakr_status add_expansion(pakr_planner *p, cudaGraph_t g, cudaGraphNode_t dep, float bound, uint64_t seed, int mode,
                           NnKind kind, cudaGraphNode_t *sample_node, cudaGraphNode_t *last)
 {
-    const bool cond = kind == NN_SELECT && p->T.XT != nullptr;
-    cudaGraphConditionalHandle h[2]{};
-    if (cond) {
-        CUDA_TRY(cudaGraphConditionalHandleCreate(&h[0], g, 0, cudaGraphCondAssignDefault));
-        CUDA_TRY(cudaGraphConditionalHandleCreate(&h[1], g, 0, cudaGraphCondAssignDefault));
-    }
     pakr_status st = capture_one(
-        p, g, dep,
-        [&](cudaStream_t s) { return launch_sample(p->P, p->ctl, p->W, p->L, bound, seed, mode, s, cond ? h : nullptr); },
+        p, g, dep, [&](cudaStream_t s) { return launch_sample(p->P, p->ctl, p->W, p->L, bound, seed, mode, s); },
         sample_node);
     if (st != PAKR_OK)
         return st;
     cudaGraphNode_t at = *sample_node;
-    if (cond) {
-        st = add_if(p, g, at, h[0],
-                    [&](cudaStream_t s) { return launch_nn_fp32(p->P, p->ctl, p->T, p->W, p->L, s); }, &at);
-        if (st != PAKR_OK)
-            return st;
-        st = add_if(p, g, at, h[1],
-                    [&](cudaStream_t s) { return launch_nn_tc(p->P, p->ctl, p->T, p->W, p->L, s); }, &at);
-    } else if (kind == NN_ONLY_TC) {
-        st = capture_one(p, g, at, [&](cudaStream_t s) { return launch_nn_tc(p->P, p->ctl, p->T, p->W, p->L, s); },
+    const DevProblem Pn = nn_problem(p, kind == NN_ONLY_TC);
+    if (kind == NN_ONLY_TC)
+        st = capture_one(p, g, at, [&](cudaStream_t s) { return launch_nn_tc(Pn, p->ctl, p->T, p->W, p->L, s); },
                          &at);
-    } else {
-        st = capture_one(p, g, at, [&](cudaStream_t s) { return launch_nn_fp32(p->P, p->ctl, p->T, p->W, p->L, s); },
+    else
+        st = capture_one(p, g, at, [&](cudaStream_t s) { return launch_nn_fp32(Pn, p->ctl, p->T, p->W, p->L, s); },
                          &at);
-    }
     if (st != PAKR_OK)
         return st;
     st = capture_one(p, g, at, [&](cudaStream_t s) { return launch_propagate(p->P, p->ctl, p->T, p->W, p->L, s); },
@@ -610,45 +598,47 @@ pakr_status build_plan_graph(pakr_planner *p)
     return PAKR_OK;
 }
 
-pakr_status build_expand_graph(pakr_planner *p)
+pakr_status build_expand_graph(pakr_planner *p, bool tc)
 {
-    if (p->expand_exec)
+    if (p->expand_exec[tc])
         return PAKR_OK;
     cudaGraph_t g = nullptr;
     CUDA_TRY(cudaGraphCreate(&g, 0));
     cudaGraphNode_t sample_node = nullptr, last = nullptr;
-    pakr_status st = add_expansion(p, g, nullptr, 0.f, 0ull, MODE_EXPAND, NN_SELECT, &sample_node, &last);
+    pakr_status st = add_expansion(p, g, nullptr, 0.f, 0ull, MODE_EXPAND, tc ? NN_ONLY_TC : NN_ONLY_FP32, &sample_node,
+                                   &last);
     if (st != PAKR_OK) {
         cudaGraphDestroy(g);
         return st;
     }
     cudaGraphExec_t exec = nullptr;
     CUDA_TRY(cudaGraphInstantiate(&exec, g, 0));
-    p->expand_graph = g;
-    p->expand_exec = exec;
-    p->expand_sample = sample_node;
+    p->expand_graph[tc] = g;
+    p->expand_exec[tc] = exec;
+    p->expand_sample[tc] = sample_node;
     return PAKR_OK;
 }
 
-// One expansion through the graph: the sample node's bound and seed arguments are
-// replaced (a host-side update of the instantiated graph), then one graph launch.
-pakr_status launch_expand_graph(pakr_planner *p, float bound, uint64_t seed)
+// One expansion through the graph of the chosen nearest-neighbour kernel: the sample node's
+// bound and seed arguments are replaced (a host-side update of the instantiated graph), then
+// one graph launch.
+pakr_status launch_expand_graph(pakr_planner *p, float bound, uint64_t seed, bool tc)
 {
-    pakr_status st = build_expand_graph(p);
+    pakr_status st = build_expand_graph(p, tc);
     if (st != PAKR_OK)
         return st;
     cudaKernelNodeParams kp{};
-    CUDA_TRY(cudaGraphKernelNodeGetParams(p->expand_sample, &kp));
-    void *args[16];
+    CUDA_TRY(cudaGraphKernelNodeGetParams(p->expand_sample[tc], &kp));
+    void *args[kSampleArgs];
     unsigned long long seed_arg = seed;
-    for (int i = 0; i < 9; ++i)
+    for (int i = 0; i < kSampleArgs; ++i)
         args[i] = kp.kernelParams[i];
     args[kSampleArgBound] = &bound;
     args[kSampleArgSeed] = &seed_arg;
     kp.kernelParams = args;
     kp.extra = nullptr;
-    CUDA_TRY(cudaGraphExecKernelNodeSetParams(p->expand_exec, p->expand_sample, &kp));
-    CUDA_TRY(cudaGraphLaunch(p->expand_exec, p->stream));
+    CUDA_TRY(cudaGraphExecKernelNodeSetParams(p->expand_exec[tc], p->expand_sample[tc], &kp));
+    CUDA_TRY(cudaGraphLaunch(p->expand_exec[tc], p->stream));
     return PAKR_OK;
 }
 
@@ -656,6 +646,7 @@ pakr_status read_ctl(pakr_planner *p)
 {
     CUDA_TRY(cudaMemcpyAsync(p->ctl_host, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, p->stream));
     CUDA_TRY(cudaStreamSynchronize(p->stream));
+    p->n_upper = p->ctl_host->count;
     return PAKR_OK;
 }
 
@@ -991,10 +982,12 @@ void pakr_destroy(pakr_planner *p)
         cudaGraphExecDestroy(p->plan_exec);
     if (p->plan_graph)
         cudaGraphDestroy(p->plan_graph);
-    if (p->expand_exec)
-        cudaGraphExecDestroy(p->expand_exec);
-    if (p->expand_graph)
-        cudaGraphDestroy(p->expand_graph);
+    for (int k = 0; k < 2; ++k) {
+        if (p->expand_exec[k])
+            cudaGraphExecDestroy(p->expand_exec[k]);
+        if (p->expand_graph[k])
+            cudaGraphDestroy(p->expand_graph[k]);
+    }
     for (auto &pe : p->pending)
         p->pool.push_back(pe.second);
     for (auto &ev : p->pool) {
@@ -1043,8 +1036,12 @@ pakr_status pakr_expand(pakr_planner *p, float cost_bound, uint64_t seed, pakr_e
         return fail(PAKR_ERR_INVALID_ARG, "cost_bound is NaN");
     DeviceGuard guard(p->device);
     // per-kernel timing needs events between the launches: plain launches then
-    pakr_status st = p->profiling ? enqueue_expand(p, cost_bound, seed) : launch_expand_graph(p, cost_bound, seed);
-    if (st != PAKR_OK || !info)
+    const bool tc = use_tc_nn(p);
+    pakr_status st = p->profiling ? enqueue_expand(p, cost_bound, seed, tc) : launch_expand_graph(p, cost_bound, seed, tc);
+    if (st != PAKR_OK)
+        return st;
+    p->n_upper = std::min<int64_t>(p->cap, p->n_upper + (int64_t)p->K * p->k);
+    if (!info)
         return st;
     st = read_ctl(p);
     if (st != PAKR_OK)
@@ -1251,6 +1248,7 @@ pakr_status pakr_tree_truncate(pakr_planner *p, int64_t count)
         return fail(PAKR_ERR_INVALID_ARG, "count %lld outside [1, tree_cap]", (long long)count);
     DeviceGuard guard(p->device);
     CUDA_TRY(launch_truncate(p->ctl, (int)count, p->stream));
+    p->n_upper = std::min<int64_t>(p->n_upper, count);
     return PAKR_OK;
 }
 
@@ -1304,6 +1302,7 @@ pakr_status pakr_tree_import(pakr_planner *p, const pakr_tree_host *t, const flo
     CUDA_TRY(cudaMemcpyAsync(p->ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, p->stream));
     CUDA_TRY(launch_import_fcost(p->P, p->ctl, p->T, (int)n, p->stream));
     CUDA_TRY(cudaStreamSynchronize(p->stream));
+    p->n_upper = n;
     return PAKR_OK;
 }
 

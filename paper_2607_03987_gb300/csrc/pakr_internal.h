@@ -182,13 +182,10 @@ struct LaunchCfg {
 };
 
 // Kernel launchers (pakr_kernels.cu).  Each returns the launch error.
-// nn_cond: the two IF-node handles of a graph that holds k_nn and k_nn_tc behind
-// conditionals (k_sample opens one per batch), or nullptr for plain launches.
 cudaError_t launch_sample(const DevProblem &P, Ctl *ctl, const DevWork &W, const LaunchCfg &L, float bound,
-                          unsigned long long seed, int mode, cudaStream_t s,
-                          const cudaGraphConditionalHandle *nn_cond = nullptr);
+                          unsigned long long seed, int mode, cudaStream_t s);
 // Index of the bound and seed arguments of k_sample (for updating them in a graph).
-constexpr int kSampleArgBound = 3, kSampleArgSeed = 4;
+constexpr int kSampleArgBound = 3, kSampleArgSeed = 4, kSampleArgs = 6;
 cudaError_t launch_nn(const DevProblem &P, const Ctl *ctl, const DevTree &T, const DevWork &W, const LaunchCfg &L,
                       cudaStream_t s);
 // k_nn alone (it still returns at once for trees of P.tc_min_n nodes or more).

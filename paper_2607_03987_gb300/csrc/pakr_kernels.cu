@@ -21,12 +21,8 @@ namespace pakr {
 // ---------------------------------------------------------------------------
 // Expansion kernels.
 // ---------------------------------------------------------------------------
-// In a graph whose nearest-neighbour kernels sit in IF nodes (set_cond != 0), thread 0
-// also opens exactly one of them for this batch's tree size: h_fp32 for k_nn below
-// P.tc_min_n nodes, h_tc for k_nn_tc from there.
 template <int D>
-__global__ void k_sample(DevProblem P, Ctl *ctl, DevWork W, float bound, unsigned long long seed_arg, int mode,
-                         cudaGraphConditionalHandle h_fp32, cudaGraphConditionalHandle h_tc, int set_cond)
+__global__ void k_sample(DevProblem P, Ctl *ctl, DevWork W, float bound, unsigned long long seed_arg, int mode)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long seed = (mode == MODE_EXPAND) ? seed_arg : ctl->seed;
@@ -36,11 +32,6 @@ __global__ void k_sample(DevProblem P, Ctl *ctl, DevWork W, float bound, unsigne
         if (mode == MODE_EXPAND)
             ctl->seed = seed_arg;
         begin_batch(ctl, (mode == MODE_EXPAND) ? bound : ctl->c_best);
-        if (set_cond) {
-            const bool tc = ctl->n_start >= P.tc_min_n;
-            cudaGraphSetConditional(h_fp32, tc ? 0u : 1u);
-            cudaGraphSetConditional(h_tc, tc ? 1u : 0u);
-        }
     }
 }
 
@@ -261,12 +252,10 @@ constexpr int kNnTile = 256;
 constexpr int kNnGroup = 8;
 
 cudaError_t launch_sample(const DevProblem &P, Ctl *ctl, const DevWork &W, const LaunchCfg &L, float bound,
-                          unsigned long long seed, int mode, cudaStream_t s, const cudaGraphConditionalHandle *nn_cond)
+                          unsigned long long seed, int mode, cudaStream_t s)
 {
-    const cudaGraphConditionalHandle h0 = nn_cond ? nn_cond[0] : cudaGraphConditionalHandle{};
-    const cudaGraphConditionalHandle h1 = nn_cond ? nn_cond[1] : cudaGraphConditionalHandle{};
     PAKR_DISPATCH_DYN(P.dyn, (k_sample<Dims<DYN_>::D><<<L.sample_blocks, L.sample_threads, 0, s>>>(
-                                 P, ctl, W, bound, seed, mode, h0, h1, nn_cond ? 1 : 0)));
+                                 P, ctl, W, bound, seed, mode)));
     return cudaGetLastError();
 }
 
@@ -283,9 +272,9 @@ static cudaError_t launch_nn_d(const DevProblem &P, const Ctl *ctl, const DevTre
     return cudaGetLastError();
 }
 
-// Both nearest-neighbour kernels are launched when the tree keeps the packed
-// operand copy; each returns at once unless the device-side tree size is in its
-// range (k_nn below P.tc_min_n, k_nn_tc from it), so no host read is needed.
+// k_nn returns at once when the device-side tree size is P.tc_min_n or more, k_nn_tc when it
+// is below: a caller that picks one kernel for any tree size passes P with tc_min_n set past
+// (k_nn: INT_MAX) or below (k_nn_tc: 0) every size.
 cudaError_t launch_nn_fp32(const DevProblem &P, const Ctl *ctl, const DevTree &T, const DevWork &W,
                            const LaunchCfg &L, cudaStream_t s)
 {
