@@ -260,8 +260,10 @@ pakr_status pakr_plan_bounded(pakr_planner *planner, const float *x_init, const 
  * counterpart; the loop itself is Algorithm 1).  Only enqueues one small
  * kernel on cuda_stream (NULL = default stream), which should be another
  * stream than the planner's, so that it runs while the plan's graph runs; the
- * loop picks the bound up at its next iteration, and nodes and children that
- * can no longer beat it are pruned from then on.  It may be made from another
+ * loop picks the bound up at its next iteration: an offer that lowers the bound
+ * counts as a new solution of the loop, which restarts its tree from the root
+ * with the lower bound, as after one of its own (Algorithm 1; the restart is
+ * not counted in pakr_path.n_restarts).  It may be made from another
  * host thread while pakr_plan runs on this planner.
  * The kernel's GPU code is loaded at pakr_create, so the call loads nothing
  * (a first, lazy load could wait for the running plan); the caller should

@@ -1076,10 +1076,13 @@ __device__ __forceinline__ bool aox_step_warp(const DevProblem &P, Ctl *ctl, con
         const unsigned long long now = globaltimer_ns();
         bool restart = false;
         const bool found = *s_found != 0;
+        // a bound offered from outside that lowered c_best is a solution too: restart
+        const bool offered = atomicExch(&ctl->offer_restart, 0) != 0;
         if (found)
             ctl->path_seq = ctl->path_seq + 1u;
-        if (found) {
+        if (found || offered)
             restart = true;
+        if (found) {
             if (stop_at_first) {
                 stop = true;
                 ctl->plan_status = 1;
@@ -1140,6 +1143,7 @@ __device__ __forceinline__ bool aox_init_one(const DevProblem &P, Ctl *ctl, cons
     ctl->n_restarts = 0;
     ctl->path_len = 0;
     ctl->path_seq = 0u;
+    ctl->offer_restart = 0;
     ctl->err = 0;
     ctl->t_first_ns = ~0ull;
     ctl->nodes_first = -1;

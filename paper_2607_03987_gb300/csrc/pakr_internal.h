@@ -146,6 +146,7 @@ struct Ctl {
     int path_len;            // nodes on the best path (edges + 1); negative = required length when too long
     unsigned path_seq;       // odd while the AO-x step writes a new best path, even otherwise
     int plan_status;         // 0 running/budget, 1 goal at stop_at_first, 3 no eligible, -1 invalid start
+    int offer_restart;       // an offered bound lowered c_best: the AO-x step restarts the tree
 };
 
 struct PlanParams {

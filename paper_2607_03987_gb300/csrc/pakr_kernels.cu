@@ -168,8 +168,13 @@ __global__ void k_offer_bound(Ctl *ctl, const float *cost)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         const float c = *cost;
-        if (c >= 0.f && c < __int_as_float(0x7f800000))
-            atomicMin(reinterpret_cast<int *>(&ctl->c_best), __float_as_int(c));
+        if (c >= 0.f && c < __int_as_float(0x7f800000)) {
+            const int old = atomicMin(reinterpret_cast<int *>(&ctl->c_best), __float_as_int(c));
+            // a cheaper path than the loop's bound is a new AO-x solution: the loop restarts its
+            // tree at its next step, as after one of its own (Algorithm 1)
+            if (old > __float_as_int(c))
+                atomicExch(&ctl->offer_restart, 1);
+        }
     }
 }
 
