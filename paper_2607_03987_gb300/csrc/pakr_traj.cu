@@ -294,7 +294,8 @@ __global__ void __launch_bounds__(32 * kTrajWarpsPerBlock)
         for (int a = 0; a < PD; ++a)
             dd += (x[a] - xp[a]) * (x[a] - xp[a]);
         J += w.w_len * sqrtf(dd + w.len_eps * w.len_eps);
-        J += w.w_obs * warp_penalty<PD>(x, P, w, gp) * h;
+        if (w.w_obs != 0.f)
+            J += w.w_obs * warp_penalty<PD>(x, P, w, gp) * h;
     }
     float e2 = 0.f;
 #pragma unroll
@@ -413,10 +414,13 @@ __device__ __forceinline__ void traj_adjoint_warp(const DevProblem &P, const Tra
 #pragma unroll
     for (int a = 0; a < PD; ++a)
         lam[a] = 2.f * w.w_goal * (x[a] - w.goal[a]);
-    warp_penalty<PD>(x, P, w, gp);
+    // (a zero obstacle weight skips the penalty's sum over every obstacle)
+    if (w.w_obs != 0.f) {
+        warp_penalty<PD>(x, P, w, gp);
 #pragma unroll
-    for (int a = 0; a < PD; ++a)
-        lam[a] += w.w_obs * gp[a] * h;
+        for (int a = 0; a < PD; ++a)
+            lam[a] += w.w_obs * gp[a] * h;
+    }
     float xs[kCkpt + 1][D];
     for (int seg = nseg - 1; seg >= 0; --seg) {
         const int s = seg * kCkpt;
@@ -461,7 +465,7 @@ __device__ __forceinline__ void traj_adjoint_warp(const DevProblem &P, const Tra
 #pragma unroll
             for (int a = 0; a < PD; ++a)
                 lam[a] -= w.w_len * dl[a] / Ls;
-            if (n >= 1) {
+            if (n >= 1 && w.w_obs != 0.f) {
                 warp_penalty<PD>(xs[i], P, w, gp);
 #pragma unroll
                 for (int a = 0; a < PD; ++a)
