@@ -122,7 +122,7 @@ def test_tc_plan_matches_fp32(cuda_lib):
 
 
 def test_expand_graph_matches_plain_launches(cuda_lib):
-    # without profiling pakr_expand launches one graph (IF nodes pick the kernel); with
+    # without profiling pakr_expand launches one graph per nearest-neighbour kernel; with
     # profiling it launches the kernels one by one: same tree, bounds and seeds, same results
     spec = W.with_sizes(W.problem("di3", env_seed=9), K=512, k=4, cap=200_000)
     n0 = 28_500  # just below the automatic switch to the tensor-core kernel (28672 nodes)
@@ -148,6 +148,30 @@ def test_expand_graph_matches_plain_launches(cuda_lib):
         assert sa == sb and ia == ib
         for key in ("samples", "near", "outcome", "controls", "steps"):
             assert np.array_equal(da[key], db[key]), key
+
+
+def test_host_kernel_choice_is_exact_either_way(cuda_lib):
+    # the host picks the nearest-neighbour kernel from an upper bound on the tree size (exact only
+    # after a read of the control block): expansions that never read it back cross the tensor-core
+    # switch with a stale bound, and the planner forced to the FP32 kernel grows the same tree
+    spec = W.with_sizes(W.problem("di3", env_seed=9), K=512, k=4, cap=200_000)
+    n0 = 27_000
+    tree = W.prefilled_tree(spec, n0, seed=17, cost_hi=2.0)
+    out = []
+    for mode in (pakr.NN_AUTO, pakr.NN_FP32):
+        planner = pakr.Planner(W.with_sizes(spec, nn_mode=mode))
+        try:
+            planner.tree_import(tree, spec["x_goal"])
+            for bound, seed in ((np.inf, 1), (1.8, 2), (np.inf, 3), (1.2, 4), (np.inf, 5)):
+                planner.expand(bound, seed, info=False)
+            out.append(planner.tree_export())
+        finally:
+            planner.close()
+    a, b = out
+    assert a["count"] == b["count"] and a["count"] > 28672
+    n = a["count"]
+    for key in ("states", "controls", "parents", "costs", "steps"):
+        assert np.array_equal(np.asarray(a[key])[:n], np.asarray(b[key])[:n]), key
 
 
 # The benchmarked workloads at their full sizes, in the launch configuration the benchmark times
