@@ -163,6 +163,18 @@ ObstacleGrid build_obstacle_grid(const pakr_problem_desc *d, const DimInfo &di)
     return best;
 }
 
+// Pinned staging of a plan's result: the first kStageHist history entries and kStageEdges path
+// edges, copied right behind the control block.
+constexpr int kStageHist = 64, kStageEdges = 128;
+struct PlanStage {
+    unsigned long long t[kStageHist];
+    float cost[kStageHist];
+    long long iter[kStageHist];
+    float x[(kStageEdges + 1) * kMaxD];
+    float u[kStageEdges * kMaxM];
+    int steps[kStageEdges];
+};
+
 // Byte offsets of every device buffer inside one allocation.
 struct Layout {
     size_t X, U, cost, fcost, parent, steps, XT;
@@ -338,6 +350,7 @@ struct pakr_planner {
     bool owns_base = false;
     Ctl *ctl_host = nullptr;        // pinned
     PlanParams *pp_host = nullptr;  // pinned
+    PlanStage *stage_host = nullptr;  // pinned
     int64_t cap = 0;
     int K = 0, k = 0;
     int path_cap = 0, hist_cap = 0;
@@ -782,6 +795,8 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
     e = cudaMallocHost(&p->ctl_host, sizeof(Ctl));
     if (e == cudaSuccess)
         e = cudaMallocHost(&p->pp_host, sizeof(PlanParams));
+    if (e == cudaSuccess)
+        e = cudaMallocHost(&p->stage_host, sizeof(PlanStage));
     if (e != cudaSuccess)
         return cleanup(fail(PAKR_ERR_OOM, "cudaMallocHost failed: %s", cudaGetErrorString(e)));
 
@@ -1000,6 +1015,8 @@ void pakr_destroy(pakr_planner *p)
         cudaFreeHost(p->ctl_host);
     if (p->pp_host)
         cudaFreeHost(p->pp_host);
+    if (p->stage_host)
+        cudaFreeHost(p->stage_host);
     if (p->capture_stream)
         cudaStreamDestroy(p->capture_stream);
     delete p;
@@ -1110,9 +1127,29 @@ pakr_status pakr_plan_bounded(pakr_planner *p, const float *x_init, const float 
     h->c_best_init = initial_bound;
     CUDA_TRY(cudaMemcpyAsync(p->pp, h, sizeof(PlanParams), cudaMemcpyHostToDevice, p->stream));
     CUDA_TRY(cudaGraphLaunch(p->plan_exec, p->stream));
-    st = read_ctl(p);
-    if (st != PAKR_OK)
-        return st;
+    // the control block, then the first kStageHist history entries and kStageEdges path edges
+    // into pinned staging, and one synchronization: a result that fits needs no second one
+    PlanStage *sg = p->stage_host;
+    const int d = p->di.d, m = p->di.m;
+    const int sh = std::min(kStageHist, p->hist_cap), se = std::min(kStageEdges, p->path_cap);
+    CUDA_TRY(cudaMemcpyAsync(p->ctl_host, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, p->stream));
+    if (sh > 0) {
+        CUDA_TRY(cudaMemcpyAsync(sg->t, p->B.hist_t, sizeof(unsigned long long) * sh, cudaMemcpyDeviceToHost,
+                                 p->stream));
+        CUDA_TRY(cudaMemcpyAsync(sg->cost, p->B.hist_cost, sizeof(float) * sh, cudaMemcpyDeviceToHost, p->stream));
+        CUDA_TRY(cudaMemcpyAsync(sg->iter, p->B.hist_iter, sizeof(long long) * sh, cudaMemcpyDeviceToHost,
+                                 p->stream));
+    }
+    CUDA_TRY(cudaMemcpyAsync(sg->x, p->B.path_x, sizeof(float) * d * (size_t)(se + 1), cudaMemcpyDeviceToHost,
+                             p->stream));
+    if (se > 0) {
+        CUDA_TRY(cudaMemcpyAsync(sg->u, p->B.path_u + m, sizeof(float) * m * (size_t)se, cudaMemcpyDeviceToHost,
+                                 p->stream));
+        CUDA_TRY(cudaMemcpyAsync(sg->steps, p->B.path_steps + 1, sizeof(int) * (size_t)se, cudaMemcpyDeviceToHost,
+                                 p->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    p->n_upper = p->ctl_host->count;
     const Ctl &c = *p->ctl_host;
     out->cost = c.n_solutions > 0 ? c.sol_best : INFINITY;
     out->n_solutions = c.n_solutions;
@@ -1128,7 +1165,13 @@ pakr_status pakr_plan_bounded(pakr_planner *p, const float *x_init, const float 
     if (c.plan_status == -1)
         return fail(PAKR_ERR_INVALID_ARG, "x_init is not a valid state (outside the state box or in an obstacle)");
     const int nh = std::min(std::min(c.n_solutions, p->hist_cap), out->max_history);
-    if (nh > 0) {
+    if (nh > 0 && nh <= sh) {
+        for (int i = 0; i < nh; ++i) {
+            out->history_time_s[i] = (double)sg->t[i] * 1e-9;
+            out->history_cost[i] = sg->cost[i];
+            out->history_iteration[i] = sg->iter[i];
+        }
+    } else if (nh > 0) {
         std::vector<unsigned long long> ht(nh);
         CUDA_TRY(cudaMemcpyAsync(ht.data(), p->B.hist_t, sizeof(unsigned long long) * nh, cudaMemcpyDeviceToHost,
                                  p->stream));
@@ -1151,7 +1194,15 @@ pakr_status pakr_plan_bounded(pakr_planner *p, const float *x_init, const float 
         if (edges > out->max_edges)
             return fail(PAKR_ERR_INVALID_ARG, "best path has %d edges, more than max_edges %d", edges,
                         out->max_edges);
-        const int d = p->di.d, m = p->di.m;
+        if (edges <= se) {
+            if (out->states)
+                memcpy(out->states, sg->x, sizeof(float) * d * (size_t)(edges + 1));
+            if (edges > 0) {
+                memcpy(out->controls, sg->u, sizeof(float) * m * (size_t)edges);
+                memcpy(out->steps, sg->steps, sizeof(int) * (size_t)edges);
+            }
+            return PAKR_GOAL_REACHED;
+        }
         CUDA_TRY(cudaMemcpyAsync(out->states, p->B.path_x, sizeof(float) * d * (size_t)(edges + 1),
                                  cudaMemcpyDeviceToHost, p->stream));
         if (edges > 0) {

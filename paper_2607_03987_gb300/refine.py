@@ -102,7 +102,7 @@ REFINE_WEIGHTS = dict(w_length=1.0, w_obstacle=0.05, beta=200.0, margin=0.01, w_
                       w_duration=0.0, length_eps=1e-4)
 
 
-def refine_path(planner, spec, path, x_goal, iters=15, candidates=16, step=0.5, weights=None, goal_margin=1e-4,
+def refine_path(planner, spec, path, x_goal, iters=15, candidates=16, step=0.5, weights=None, goal_margin=1e-3,
                 fused=True):
     """Shorten a path found by pakr_plan with its step counts fixed.
 
@@ -112,7 +112,8 @@ def refine_path(planner, spec, path, x_goal, iters=15, candidates=16, step=0.5, 
     descent direction at once (clamped to the control box) and keeps the
     shortest candidate that the planner's rules accept (valid after every
     substep, ending in the goal ball, here by a relative margin of goal_margin
-    inside it, so that a replay in another precision stays in) if it is shorter
+    inside it, so that a replay in another precision stays in: 1e-3 of the radius
+    covers the FP32 integration drift of a few hundred RK4 steps) if it is shorter
     than the current path.  fused: the whole loop is one pakr_traj_refine launch
     on the planner's stream; otherwise each iteration runs through TrajCost's
     autograd backward and pakr_traj_check (the same rules; the per-edge gradient
