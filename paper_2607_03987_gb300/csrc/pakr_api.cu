@@ -83,7 +83,10 @@ struct ObstacleGrid {
     std::vector<unsigned short> items;
 };
 
-constexpr int kPropSmemBudget = 46 * 1024;  // dynamic shared memory of k_propagate (default limit 48 KB)
+constexpr int kPropSmemBudget = 46 * 1024;
+// k_nn_tc, one full wave: the share of each pair's node tiles that the CTA launched first takes
+// (bench, 1M-node tree: 0.50 88.2 us, 0.52 87.0, 0.54 89.1, 0.56 91.6)
+constexpr float kTcPairShare = 0.52f;  // dynamic shared memory of k_propagate (default limit 48 KB)
 
 ObstacleGrid build_obstacle_grid(const pakr_problem_desc *d, const DimInfo &di)
 {
@@ -963,6 +966,10 @@ pakr_status pakr_create(const pakr_problem_desc *desc, pakr_planner **out)
             break;
         }
     }
+    // one full wave with an even number of chunks: pair the CTAs launched first and second
+    // (k_nn_tc), the first taking kTcPairShare of each pair's tiles
+    p->P.tc_pair_share =
+        (C.tc_chunks * C.tc_qblocks == tc_slots && C.tc_chunks % 2 == 0 && kTcCtasPerSm == 2) ? kTcPairShare : 0.f;
     const int64_t R = (int64_t)p->K * p->k;
     // Lanes per rollout: as many as fit one resident wave of k_propagate on every SM (six
     // 256-thread blocks, its register limit), but no more lanes than there are obstacle tests

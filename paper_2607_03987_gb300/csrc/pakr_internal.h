@@ -49,6 +49,9 @@ struct DevProblem {
     float tc_c[kMaxD];
     float tc_xbox2;
     float tc_s = 1.f;     // power of two the FP16 filter scales centred coordinates by (box radius to [2^7, 2^8))
+    // > 0: the tensor-core grid is one full wave of two CTAs per SM, and the CTA of each pair
+    // that is launched first takes this share of the pair's node tiles (0: equal chunks)
+    float tc_pair_share = 0.f;
     int tc_min_n = 0x7FFFFFFF;
     // obstacle grid over the position box (grid_g = 0: none, every obstacle is tested): cell
     // index per position axis a is obstacle_cell(p_a, grid_lo[a], grid_inv[a], grid_g), cells

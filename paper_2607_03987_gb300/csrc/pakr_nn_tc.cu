@@ -101,9 +101,28 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
         return;  // small trees take k_nn
     // the chunk: whole half tiles of 128 nodes
     const int ntile_all = (n + kTcBN - 1) / kTcBN;
-    const int tiles_per = (ntile_all + gridDim.x - 1) / gridDim.x;
-    const int tile0 = blockIdx.x * tiles_per;
-    const int ntiles = min(ntile_all, tile0 + tiles_per) - tile0;
+    int tile0, ntiles, qblock;
+    if (P.tc_pair_share > 0.f) {
+        // One full wave, two CTAs per SM: the CTAs launched second (the upper half of the linear
+        // block order) stream about 8 % slower than the first.  Each query block takes half of
+        // its CTAs from each half, in pairs over one node range, split in favour of the first.
+        const int lin = blockIdx.y * gridDim.x + blockIdx.x;
+        const int n_first = (gridDim.x * gridDim.y) / 2;
+        const bool later = lin >= n_first;
+        const int r = later ? lin - n_first : lin;
+        const int pairs = gridDim.x / 2;  // pairs per query block
+        qblock = r / pairs;
+        const int per_pair = (ntile_all + pairs - 1) / pairs;
+        const int p0 = min(ntile_all, (r % pairs) * per_pair), p1 = min(ntile_all, p0 + per_pair);
+        const int a = min(p1 - p0, (int)((float)(p1 - p0) * P.tc_pair_share + 0.5f));
+        tile0 = later ? p0 + a : p0;
+        ntiles = later ? p1 - p0 - a : a;
+    } else {
+        const int tiles_per = (ntile_all + gridDim.x - 1) / gridDim.x;
+        tile0 = blockIdx.x * tiles_per;
+        ntiles = min(ntile_all, tile0 + tiles_per) - tile0;
+        qblock = blockIdx.y;
+    }
     if (ntiles <= 0)
         return;
     const int start = tile0 * kTcBN;
@@ -112,7 +131,7 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
     const bool flagged = ctl->tc_flag != 0;
     const int K = P.K;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int qbase = blockIdx.y * kTcM;
+    const int qbase = qblock * kTcM;
     const unsigned long long kWaitNs = 1000000000ull;
 
     // ---- setup: TMEM, barriers, the query operand ----
