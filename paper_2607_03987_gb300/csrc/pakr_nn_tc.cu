@@ -12,7 +12,9 @@
 // the bound of tc_bound_coef on |a + |q - c|^2 - e|).  After the chunk, every node whose
 // exact distance could be the row's minimum lies in a remembered group (its filter value is
 // at most m1 + band), so recomputing e from the tree's FP32 coordinates on those groups gives
-// the exact argmin.  A row whose candidate ring overflowed or whose query lies outside the
+// the exact argmin; the whole CTA does that last step, sixteen threads per (row, group) pair,
+// so that the loads of all groups are in flight together.  A row whose candidate ring
+// overflowed or whose query lies outside the
 // filter's range, or a tree flagged as leaving the box bound, is rescanned exactly by the
 // whole CTA.  Chunk results merge with a 64-bit atomicMin of (distance bits << 32 | index),
 // as in k_nn.  Since a differs from the distance by a per-query constant, the chunks also
@@ -21,7 +23,9 @@
 // Two CTAs share an SM, each with two accumulators of 128 TMEM columns.  Within a CTA the
 // work is one dependency chain (MMA, commit, readers, release, next MMA) whose mbarrier
 // hand-offs cost on the order of a hundred cycles each; the second CTA's MMAs fill the
-// tensor pipe while the first waits on that chain.
+// tensor pipe while the first waits on that chain.  With P.tc_pair_share > 0 (one full wave)
+// the CTAs launched first and second are paired on one node range and the first takes that
+// share of it: the second CTA on an SM streams slower.
 //
 // Roles (TcShape<D>::THREADS: 12 warps per CTA for d <= 8, 8 for larger d):
 //   warp 0 lane 0   bulk-copies packed half tiles (T.XT) and f-costs into a ring of stages;
