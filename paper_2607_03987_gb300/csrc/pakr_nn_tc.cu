@@ -399,11 +399,7 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
             // the group minima come straight from the TMEM loads (min reduction, sm_103a): one
             // load per 16-node group, no ALU work on the values
             float m[NG];
-#pragma unroll
-            for (int h = 0; h < NG; ++h) {
-                __syncwarp();
-                m[h] = tmem_ldred_min16(tcol + 16 * h);
-            }
+            tmem_ldred_groups<NG, S::LD_BATCH>(tcol, m);
             tc_fence_before();
             __syncwarp();
             if (lane == 0)

@@ -181,6 +181,43 @@ __device__ __forceinline__ float tmem_ldred_min16(uint32_t taddr)
                  : "memory");
     return m;
 }
+// The minima of two 16-column groups (at taddr and taddr + 16) from two reducing loads that
+// are in flight together, with one wait for both.
+__device__ __forceinline__ void tmem_ldred_min16x2(uint32_t taddr, float &m0, float &m1)
+{
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.red.sync.aligned.32x32b.x16.min.f32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, %32, [%34];\n\t"
+                 "tcgen05.ld.red.sync.aligned.32x32b.x16.min.f32 "
+                 "{%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, %33, [%35];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=f"(m0), "=f"(m1)
+                 : "r"(taddr), "r"(taddr + 16u)
+                 : "memory");
+}
+// Minima of NG consecutive 16-column groups, BATCH (1 or 2) loads in flight per wait.
+template <int NG, int BATCH>
+__device__ __forceinline__ void tmem_ldred_groups(uint32_t taddr, float (&m)[NG])
+{
+    static_assert(BATCH == 1 || (BATCH == 2 && NG % 2 == 0), "load batch");
+    if constexpr (BATCH == 2) {
+#pragma unroll
+        for (int h = 0; h < NG; h += 2) {
+            __syncwarp();
+            tmem_ldred_min16x2(taddr + 16u * h, m[h], m[h + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int h = 0; h < NG; ++h) {
+            __syncwarp();
+            m[h] = tmem_ldred_min16(taddr + 16u * h);
+        }
+    }
+}
 // Shared-memory matrix descriptor, no swizzle, K-major: LBO = byte distance of
 // the two core matrices along K, SBO = byte distance of 8-row groups.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
@@ -253,6 +290,10 @@ struct TcShape {
     static constexpr int RH = D <= 8 ? 2 : 1;
     static constexpr int READERS = 128 * RH;
     static constexpr int THREADS = kTcReader0 * 32 + READERS;
+    // TMEM loads a reader keeps in flight per wait: two where the launch leaves 128 registers
+    // a thread (d > 8: quadrotor 333 -> 327 us at n = 1,000,000), one for d <= 8, where the
+    // second load's destination registers spill at 80 (d = 6: 87.3 -> 90.3 us)
+    static constexpr int LD_BATCH = D <= 8 ? 1 : 2;
     static constexpr int RING_BYTES = kTcRing * READERS * 8;
     // two CTAs per SM: each within half of the SM's 228 KB, static shared memory included
     static constexpr int NSTAGE_FIT = (100 * 1024 - A_BYTES - RING_BYTES) / (STAGE_BYTES + F_BYTES);
