@@ -83,10 +83,10 @@ struct ObstacleGrid {
     std::vector<unsigned short> items;
 };
 
-constexpr int kPropSmemBudget = 46 * 1024;
+constexpr int kPropSmemBudget = 46 * 1024;  // dynamic shared memory of k_propagate (default limit 48 KB)
 // k_nn_tc, one full wave: the share of each pair's node tiles that the CTA launched first takes
 // (bench, 1M-node tree: 0.50 88.2 us, 0.52 87.0, 0.54 89.1, 0.56 91.6)
-constexpr float kTcPairShare = 0.52f;  // dynamic shared memory of k_propagate (default limit 48 KB)
+constexpr float kTcPairShare = 0.52f;
 
 ObstacleGrid build_obstacle_grid(const pakr_problem_desc *d, const DimInfo &di)
 {
