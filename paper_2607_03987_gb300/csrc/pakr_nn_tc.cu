@@ -36,8 +36,9 @@
 //                   (tcgen05.ld.red min, sm_103a) and keep candidate rings: for d <= 8 two
 //                   warps per TMEM lane quarter, 64 columns each (two reader threads per query
 //                   row); for larger d one per quarter, all 128 columns.
-// Warps off the MMA thread's chain wait with the suspending mbarrier.try_wait, so that their
-// polls take no issue slots from the readers.  Every wait is bounded (1 s of device time);
+// Every role, the MMA thread included, waits with the suspending mbarrier.try_wait: a hop
+// takes about as long as with a polling test_wait, and the waits take no issue slots from the
+// readers on the same scheduler.  Every wait is bounded (1 s of device time);
 // on timeout the CTA sets ERR_TC_TIMEOUT and stops issuing work.  Before the CTA frees its
 // TMEM and leaves, the loader waits (bounded) until every bulk copy it issued has landed and
 // the MMA thread waits (bounded) on a final commit that follows every MMA it issued, so no
@@ -317,8 +318,8 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
                         break;
                     // the accumulator has been read (tile t + ac - 2's; usually the longer wait,
                     // so it comes first), and the stage is masked
-                    if ((t > 0 && !mbar_wait_bounded(empty0 + 8 * ac, epar ^ 1u, kWaitNs)) ||
-                        !mbar_wait_bounded(full0 + st8, fpar, kWaitNs)) {
+                    if ((t > 0 && !mbar_wait_suspend(empty0 + 8 * ac, epar ^ 1u, kWaitNs)) ||
+                        !mbar_wait_suspend(full0 + st8, fpar, kWaitNs)) {
                         s_abort = 1;
                         atomicOr(&ctl->err, ERR_TC_TIMEOUT);
                         live = false;
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
             // still writes the accumulators when TMEM is freed, also after an abort that left
             // accumulators unread.
             mma_commit(smem_u32(&s_drain));
-            if (!mbar_wait_bounded(smem_u32(&s_drain), 0, kWaitNs)) {
+            if (!mbar_wait_suspend(smem_u32(&s_drain), 0, kWaitNs)) {
                 s_abort = 1;
                 atomicOr(&ctl->err, ERR_TC_TIMEOUT);
             }

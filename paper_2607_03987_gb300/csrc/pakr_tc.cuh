@@ -78,26 +78,6 @@ __device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity)
                  : "memory");
     return ok != 0;
 }
-// Wait for the phase with the given parity for at most limit_ns of device
-// time; false on timeout.  Polls with the non-blocking test; after 64 failed
-// polls the thread sleeps between polls (32 ns doubling to 256 ns).
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, unsigned long long limit_ns)
-{
-    if (mbar_test_wait(bar, parity))
-        return true;
-    const unsigned long long t0 = tc_clock_ns();
-    unsigned ns = 32;
-    for (int it = 0;; ++it) {
-        if (mbar_test_wait(bar, parity))
-            return true;
-        if (it >= 64) {
-            __nanosleep(ns);
-            ns = ns < 256 ? 2 * ns : 256;
-        }
-        if ((it & 15) == 15 && tc_clock_ns() - t0 > limit_ns)
-            return false;
-    }
-}
 // Potentially blocking test of the phase: the thread is suspended until the phase
 // completes or a hardware time limit passes, so a waiting warp issues nothing.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
@@ -111,9 +91,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
                  : "memory");
     return ok != 0;
 }
-// Wait for the phase for at most limit_ns of device time without spinning: for the warps
-// that are not on the tensor pipe's critical path, whose polls would take issue slots and
-// ALU cycles from the accumulator readers on the same scheduler.
+// Wait for the phase with the given parity for at most limit_ns of device time (false on
+// timeout) without spinning: polls would take issue slots and ALU cycles from the accumulator
+// readers on the same scheduler, and a suspended thread wakes about as soon after the phase
+// completes as a polling one sees it.
 __device__ __forceinline__ bool mbar_wait_suspend(uint32_t bar, uint32_t parity, unsigned long long limit_ns)
 {
     if (mbar_test_wait(bar, parity))
