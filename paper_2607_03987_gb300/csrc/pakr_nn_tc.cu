@@ -379,62 +379,72 @@ __global__ void __launch_bounds__(TcShape<D>::THREADS, kTcCtasPerSm)
         // to be used one period later so that the load never stalls the loop.
         const bool pub = W.nn_amin != nullptr && qid < K && !s_ovf[qrow];  // (a row out of range publishes nothing)
         unsigned gkey = 0xFFFFFFFFu;
-        for (int t = 0; t < ntiles; ++t) {
-            const int b = t % kTcAcc;
-            const bool ok =
-                __all_sync(0xFFFFFFFFu, mbar_wait_suspend(smem_u32(&s_done[b]), (t / kTcAcc) & 1, kWaitNs));
-            if (!ok) {
-                if (lane == 0) {
-                    s_abort = 1;
-                    atomicOr(&ctl->err, ERR_TC_TIMEOUT);
+        constexpr int CW = kTcBN / S::RH;  // accumulator columns of this reader
+        constexpr int NG = CW / kTcG;      // 16-node groups it reduces per tile
+        const uint32_t tcol0 = tbase + (uint32_t)(CW * half) + ((uint32_t)(32 * quarter) << 16);
+        uint32_t dpar = 0;  // phase parity of the accumulators' ready barriers
+        // two tiles per trip, one per accumulator, so that the accumulator is a constant
+        for (int t0 = 0; t0 < ntiles; t0 += kTcAcc) {
+            bool stop = false;
+#pragma unroll
+            for (int b = 0; b < kTcAcc; ++b) {
+                const int t = t0 + b;
+                if (t >= ntiles)
+                    break;
+                const bool ok = __all_sync(0xFFFFFFFFu, mbar_wait_suspend(smem_u32(&s_done[b]), dpar, kWaitNs));
+                if (!ok) {
+                    if (lane == 0) {
+                        s_abort = 1;
+                        atomicOr(&ctl->err, ERR_TC_TIMEOUT);
+                    }
+                    stop = true;
+                    break;
                 }
-                break;
-            }
-            tc_fence_after();
-            constexpr int CW = kTcBN / S::RH;  // accumulator columns of this reader
-            constexpr int NG = CW / kTcG;      // 16-node groups it reduces per tile
-            const uint32_t tcol = tbase + (uint32_t)(b * kTcBN + CW * half) + ((uint32_t)(32 * quarter) << 16);
-            const int gbase = start + t * kTcBN + CW * half;
-            // minima of this reader's 16-node groups, then the accumulator is released; one branch
-            // per tile (the candidate test rarely passes once the running minimum has settled)
-            // the group minima come straight from the TMEM loads (min reduction, sm_103a): one
-            // load per 16-node group, no ALU work on the values
-            float m[NG];
-            tmem_ldred_groups<NG, S::LD_BATCH>(tcol, m);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0)
-                mbar_arrive(smem_u32(&s_empty[b]));
-            if ((t & 31) == 31 && pub) {
-                const float g = tc_unord(gkey);  // the value read one period ago
-                if (g < m1)
-                    thr = fminf(thr, g + band);
-                if (m1 < kTcEligible)
-                    atomicMin(W.nn_amin + qid, tc_ord(m1));
-                gkey = __ldcg(W.nn_amin + qid);
-            }
-            float mm = m[0];
+                tc_fence_after();
+                // minima of this reader's 16-node groups, then the accumulator is released; one
+                // branch per tile (the candidate test rarely passes once the running minimum has
+                // settled); the group minima come straight from the TMEM loads (min reduction,
+                // sm_103a): one load per 16-node group, no ALU work on the values
+                float m[NG];
+                tmem_ldred_groups<NG, S::LD_BATCH>(tcol0 + (uint32_t)(b * kTcBN), m);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(smem_u32(&s_empty[b]));
+                if ((t & 31) == 31 && pub) {
+                    const float g = tc_unord(gkey);  // the value read one period ago
+                    if (g < m1)
+                        thr = fminf(thr, g + band);
+                    if (m1 < kTcEligible)
+                        atomicMin(W.nn_amin + qid, tc_ord(m1));
+                    gkey = __ldcg(W.nn_amin + qid);
+                }
+                float mm = m[0];
 #pragma unroll
-            for (int h = 1; h < NG; ++h)
-                mm = fminf(mm, m[h]);
-            if (mm <= thr) {
+                for (int h = 1; h < NG; ++h)
+                    mm = fminf(mm, m[h]);
+                if (mm <= thr) {
 #pragma unroll
-                for (int h8 = 0; h8 < NG; ++h8) {
-                    if (m[h8] <= thr) {
-                        if (m[h8] < m1) {
-                            m1 = m[h8];
-                            thr = fminf(thr, m1 + band);
+                    for (int h8 = 0; h8 < NG; ++h8) {
+                        if (m[h8] <= thr) {
+                            if (m[h8] < m1) {
+                                m1 = m[h8];
+                                thr = fminf(thr, m1 + band);
+                            }
+                            const int slot = pos & (kTcRing - 1);
+                            // an entry still within the band would be lost: the row falls back to a rescan
+                            if (pos >= kTcRing && ring_val[slot * S::READERS + e] <= thr)
+                                ovf = 1;
+                            ring_val[slot * S::READERS + e] = m[h8];
+                            ring_grp[slot * S::READERS + e] = start + t * kTcBN + CW * half + 16 * h8;
+                            ++pos;
                         }
-                        const int slot = pos & (kTcRing - 1);
-                        // an entry still within the band would be lost: the row falls back to a rescan
-                        if (pos >= kTcRing && ring_val[slot * S::READERS + e] <= thr)
-                            ovf = 1;
-                        ring_val[slot * S::READERS + e] = m[h8];
-                        ring_grp[slot * S::READERS + e] = gbase + 16 * h8;
-                        ++pos;
                     }
                 }
             }
+            if (stop)
+                break;
+            dpar ^= 1u;
         }
         if (pub && m1 < kTcEligible)
             atomicMin(W.nn_amin + qid, tc_ord(m1));
