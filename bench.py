@@ -133,9 +133,10 @@ def measured_peaks():
 # dram__bytes_read.sum + dram__bytes_write.sum of one tensor-core nearest-neighbour launch
 # (k_nn_tc) on the bench workload (n = 1,000,000 nodes, d = 6), from the ncu capture named in
 # NN_DRAM_SOURCE.  None when the kernel has changed since that capture.
-NN_DRAM_BYTES_NCU = 36.886528e6 + 1024.0
+NN_DRAM_BYTES_NCU = 36.885248e6 + 3584.0
 NN_DRAM_SOURCE = ("profiles/k_nn_tc_di3_n1M.md, current kernel (FP16 operands, CTA-wide resolve, paired "
-                  "chunks, suspending waits in every role): dram__bytes_read.sum + dram__bytes_write.sum "
+                  "chunks, suspending waits in every role, readers two tiles per trip): dram__bytes_read.sum + "
+                  "dram__bytes_write.sum "
                   "of one launch")
 
 # Bytes of the planner's device control block that pakr_expand and pakr_plan read back.
