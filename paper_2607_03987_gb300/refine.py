@@ -323,9 +323,15 @@ def refined_aox_live(planner, ref_planner, spec, budget_s, seed=0, refine_iters=
         planner.plan_snapshot(st, ct, sp, info, side)
         info.cpu()
     side.synchronize()
-    res = []
-    th = threading.Thread(target=lambda: res.append(planner.plan(spec["x_init"], spec["x_goal"], budget_s=budget_s,
-                                                                 seed=seed)))
+    res, err = [], []
+
+    def run_plan():
+        try:
+            res.append(planner.plan(spec["x_init"], spec["x_goal"], budget_s=budget_s, seed=seed))
+        except BaseException as e:  # re-raised on this thread once the plan has ended
+            err.append(e)
+
+    th = threading.Thread(target=run_plan)
     t0 = time.perf_counter()
     th.start()
     seen, best_ref, best_path, gain = 0, float("inf"), None, 0.0
@@ -362,6 +368,8 @@ def refined_aox_live(planner, ref_planner, spec, budget_s, seed=0, refine_iters=
         else:
             time.sleep(poll_s)
     th.join()
+    if err:
+        raise err[0]
     r = res[0]
     own = float(r["cost"]) if r["n_solutions"] else float("inf")
     if best_ref < own:
