@@ -66,3 +66,42 @@ def test_reference_arm_other_ranks_do_nothing():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                           "--warmup", "0"], capture_output=True, text=True, timeout=120, cwd=ROOT, env=env)
     assert out.returncode == 0 and out.stdout.strip() == ""
+
+
+def test_work_counts():
+    """The roofline's work and byte counts: 3 K n d flops (a subtract, a multiply and an add
+    per coordinate of every query-node pair) and n (d + 1) 4-byte words per pass."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.nn_flops_per_launch(1024, 1_000_000, 6) == 3 * 1024 * 1_000_000 * 6
+    assert bench.nn_bytes_per_launch(1_000_000, 6) == 28_000_000
+    # as issued: 1024 queries in 8 blocks of 128, 1,000,000 nodes padded to 3907 tiles of 256,
+    # two K = 16 MMAs per 128 x 128 block
+    assert bench.nn_tc_mma_flops_per_launch(1024, 1_000_000, 6, 16, 2) == 2.0 * 1024 * 3907 * 256 * 16 * 2
+    assert bench.nn_tc_filter_flops_per_launch(1024, 1_000_000, 6, 16) == 2.0 * 1024 * 1_000_000 * 16
+
+
+def test_tc_shape_matches_the_kernel(tmp_path):
+    """bench.tc_shape (packed row width, MMAs per stage) agrees with the kernel's TcShape."""
+    nvcc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    sys.path.insert(0, ROOT)
+    import bench
+
+    dims = (3, 4, 5, 6, 12)
+    src = tmp_path / "shape.cu"
+    body = "".join(f'    std::printf("%d %d %d\\n", {d}, pakr::TcShape<{d}>::KT, pakr::TcShape<{d}>::MMAS);\n'
+                   for d in dims)
+    src.write_text('#include <cstdio>\n#include "pakr_tc.cuh"\nint main()\n{\n' + body + "    return 0;\n}\n")
+    exe = tmp_path / "shape"
+    csrc = os.path.join(ROOT, "paper_2607_03987_gb300", "csrc")
+    r = subprocess.run([nvcc, "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-I", csrc, "-I",
+                        os.path.join(ROOT, "include"), str(src), "-o", str(exe)], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    got = {int(a): (int(b), int(c)) for a, b, c in (ln.split() for ln in out.stdout.split("\n") if ln.strip())}
+    assert got == {d: bench.tc_shape(d) for d in dims}
