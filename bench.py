@@ -13,7 +13,7 @@ propagate-collide kernel (FP32 ALU bound), the e2e rate through the C ABI with
 the per-step info read back to the host, p50 time to first solution and the
 AO-x cost after 100 ms on the three planning workloads (with a cost-vs-time
 curve), the batched, adjoint and refinement measurements, a reduced Table 4
-sweep, the CPU oracle timed on a bounded sample (one thread and all host
+sweep, expansions/s on a tree from real growth, the CPU oracle timed on a bounded sample (one thread and all host
 cores), and clocks.  Everything that runs the oracle sits in the CPU leg at
 the end (timing, and the oracle's checks of gradients and paths).
 
@@ -135,9 +135,8 @@ def measured_peaks():
 # NN_DRAM_SOURCE.  None when the kernel has changed since that capture.
 NN_DRAM_BYTES_NCU = 36.885248e6 + 3584.0
 NN_DRAM_SOURCE = ("profiles/k_nn_tc_di3_n1M.md, current kernel (FP16 operands, CTA-wide resolve, paired "
-                  "chunks, suspending waits in every role, readers two tiles per trip): dram__bytes_read.sum + "
-                  "dram__bytes_write.sum "
-                  "of one launch")
+                  "chunks, suspending waits in every role, readers two tiles per trip): "
+                  "dram__bytes_read.sum + dram__bytes_write.sum of one launch")
 
 # Bytes of the planner's device control block that pakr_expand and pakr_plan read back.
 CTL_BYTES = 216
@@ -418,6 +417,64 @@ def tree_size_sweep(dev, stream, steps=10, warmup=3):
         out.sort(key=lambda r: (r["workload"], r["n"]))
         del tree
     return out
+
+
+def grown_tree_expansions(dev, stream, steps=10, warmup=3, max_expansions=600):
+    """Expansions/s on a snapshot of a tree from real growth (the other fixed-size trees are
+    prefilled uniformly): the benchmark workload's tree grown from the start by plain
+    expansions under an infinite bound until it holds N_PREFILL nodes, then expanded from its
+    first N_PREFILL nodes (truncated back before every step, L2 flushed before every timed
+    step), as in the tree-size sweep."""
+    import torch
+
+    from paper_2607_03987_gb300 import pakr
+    from paper_2607_03987_gb300 import workloads as W
+
+    spec = W.problem(WORKLOAD, env_seed=0)
+    R = spec["K"] * spec["k"]
+    planner = pakr.Planner(spec, device=dev, stream=stream)
+    try:
+        planner.tree_reset(spec["x_init"], spec["x_goal"])
+        n, grown = 1, 0
+        while n < N_PREFILL and grown < max_expansions:
+            planner.expand(np.inf, 70_000 + grown, info=False)
+            grown += 1
+            n, _ = planner.tree_size()
+        if n < N_PREFILL:
+            return {"workload": WORKLOAD, "error": f"the tree reached {n} nodes in {grown} expansions"}
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+        for w in range(warmup):
+            planner.tree_truncate(N_PREFILL)
+            planner.expand(np.inf, 900 + w, info=False)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for s_, (a, b) in enumerate(ev):
+            planner.tree_truncate(N_PREFILL)
+            flush.zero_()
+            a.record(stream)
+            planner.expand(np.inf, s_, info=False)
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        planner.set_profiling(True)  # per-kernel times: a second pass with per-launch events
+        for s_ in range(steps):
+            planner.tree_truncate(N_PREFILL)
+            flush.zero_()
+            planner.expand(np.inf, 500 + s_, info=False)
+        kt = planner.kernel_times()
+        planner.set_profiling(False)
+        nk = "k_nn_tc" if nn_uses_tensor_cores(spec, N_PREFILL) else "k_nn"
+        nn_ms = kt[nk]["ms"] / max(kt[nk]["launches"], 1)
+        return {"workload": WORKLOAD, "n": N_PREFILL, "grown_in_expansions": grown, "parents": spec["K"],
+                "branching": spec["k"], "rollouts_per_s": R / (ms * 1e-3), "ms_per_step": ms, "nn_kernel": nk,
+                "nn_ms": nn_ms,
+                "nn_tflops": nn_flops_per_launch(spec["K"], N_PREFILL, spec["d"]) / (nn_ms * 1e-3) / 1e12,
+                "propagate_ms": kt["k_propagate"]["ms"] / max(kt["k_propagate"]["launches"], 1),
+                "append_ms": kt["k_append"]["ms"] / max(kt["k_append"]["launches"], 1),
+                "sample_ms": kt["k_sample"]["ms"] / max(kt["k_sample"]["launches"], 1),
+                "tree": "the first 1,000,000 nodes of a tree grown from the start by plain expansions under an "
+                        "infinite bound (the same problem, 1024 parents x 8 controls per expansion)"}
+    finally:
+        planner.close()
 
 
 def batched_vs_sequential(dev, stream, n_queries=256, seed=4242, max_iterations=2000, budget_s=20.0):
@@ -914,6 +971,11 @@ def main():
             pending["paths"] = {"refined_aox_100ms": p1, "refined_aox_100ms_cluttered": p2}
         if args.table4_trials > 0:
             line["table4_quad12"] = table4_sweep(dev, stream, trials=args.table4_trials)
+        if not args.no_sweep:
+            try:
+                line["grown_tree"] = grown_tree_expansions(dev, stream)
+            except Exception as e:  # a failed extra measurement leaves the rest of the line intact
+                line["grown_tree"] = {"workload": WORKLOAD, "error": f"{type(e).__name__}: {e}"}
         # ---- the CPU leg: the oracle timed on the host cores, and its checks of GPU results ----
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(spec, tree_seed=1 + rank, seed=7)

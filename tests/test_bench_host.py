@@ -105,3 +105,75 @@ def test_tc_shape_matches_the_kernel(tmp_path):
     assert out.returncode == 0, out.stderr
     got = {int(a): (int(b), int(c)) for a, b, c in (ln.split() for ln in out.stdout.split("\n") if ln.strip())}
     assert got == {d: bench.tc_shape(d) for d in dims}
+
+
+def test_grown_tree_measurement_logic(monkeypatch):
+    """bench.grown_tree_expansions on a fake planner and fake CUDA events: the tree is grown by
+    plain expansions until it holds the benchmark's node count, every timed step starts from
+    that count, and the per-kernel times come from the profiled pass alone."""
+    import torch
+
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2607_03987_gb300 import pakr
+
+    log = []
+
+    class FakePlanner:
+        def __init__(self, spec, device=0, stream=None):
+            self.n, self.prof, self.kt = 0, False, {}
+
+        def tree_reset(self, x_init, x_goal):
+            self.n = 1
+
+        def expand(self, bound, seed, info=True):
+            assert bound == float("inf")
+            log.append(("expand", self.n, self.prof))
+            self.n = min(1 << 20, self.n + 6000)
+            if self.prof:
+                for k in ("k_sample", "k_nn_tc", "k_propagate", "k_append"):
+                    e = self.kt.setdefault(k, {"ms": 0.0, "launches": 0})
+                    e["ms"] += 0.05
+                    e["launches"] += 1
+            return 0, None
+
+        def tree_size(self):
+            return self.n, 0
+
+        def tree_truncate(self, n):
+            self.n = min(self.n, n)
+
+        def set_profiling(self, on):
+            self.prof = on
+            if on:
+                self.kt = {}
+
+        def kernel_times(self):
+            return self.kt
+
+        def close(self):
+            log.append(("close",))
+
+    class Event:
+        def __init__(self, enable_timing=True):
+            pass
+
+        def record(self, stream=None):
+            pass
+
+        def elapsed_time(self, other):
+            return 0.1
+
+    empty = torch.empty
+    monkeypatch.setattr(pakr, "Planner", FakePlanner)
+    monkeypatch.setattr(torch.cuda, "Event", Event)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda dev=None: None)
+    monkeypatch.setattr(torch, "empty", lambda *a, device=None, **k: empty(16))
+    r = bench.grown_tree_expansions(0, None, steps=4, warmup=3)
+    grow = -(-(bench.N_PREFILL - 1) // 6000)
+    assert r["n"] == bench.N_PREFILL and r["grown_in_expansions"] == grow
+    timed = [e for e in log[grow:] if e[0] == "expand"]
+    assert len(timed) == 3 + 4 + 4 and all(n == bench.N_PREFILL for _, n, _ in timed)
+    assert r["ms_per_step"] == pytest.approx(0.1) and r["nn_ms"] == pytest.approx(0.05)
+    assert r["rollouts_per_s"] == pytest.approx(1024 * 8 / 0.1e-3)
+    assert log[-1] == ("close",)
